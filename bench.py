@@ -1,0 +1,345 @@
+"""Benchmark: Parareal time-to-1e-6 on one GB300, stencil GLUP/s and %HBM.
+
+One step = one full Parareal solve of the 256^3 FP32-stencil / FP64-
+correction workload (N = 32 slices, T = 1, dt_F = 1/8192, coarse RK4 on 32^3
+at 1/256, k^-2 random initial field): the coarse start-up chain, then
+iterations (batched fine sweep of all open slices, serial coarse sweep with
+the correction and norms) until the defect d^k against the serial fine
+solution is <= 1e-6.
+
+Reported ``value``: fine-stencil point updates executed in the solve per
+second (GLUP/s), inputs resident in HBM.  Beside it: the solve time
+(time-to-1e-6), the serial fine time on the same GPU, the roofline of the
+fused RK4 kernel from CUDA-event timing of its launches inside the timed
+region, the end-to-end number through the C ABI with host buffers, and the
+FP64 CPU oracle timed on this host.
+
+``--impl reference`` times the CPU oracle instead (the only reference this
+method has), on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("time-to-1e-6-error Parareal vs serial fine on 1 GB300; stencil GLUP/s, % HBM peak")
+UNIT = "GLUP/s"
+TOL = 1e-6
+KERNEL = "rk4_fused_kernel<float,64,16>"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "rk4_fused_256.md")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def stencil_hash():
+    h = hashlib.sha1()
+    with open(os.path.join(ROOT, "paper_1409_8563_gb300", "csrc", "stencil.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    or None when the summary is missing or the kernel source changed since."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    text = open(PROFILE_SUMMARY).read()
+    m = re.search(r"stencil_sha1:\s*([0-9a-f]+)", text)
+    t = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != stencil_hash():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init(n_gpus):
+    if n_gpus <= 1 or "RANK" not in os.environ:
+        return 0, 1, None
+    import torch.distributed as dist
+    dist.init_process_group("nccl")
+    return dist.get_rank(), dist.get_world_size(), dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------ CPU oracle leg
+
+def oracle_sample(n_steps, n=256):
+    """Time n_steps FP64 RK4 steps of the oracle on one 256^3 field (1 thread)."""
+    from oracle import core
+    from paper_1409_8563_gb300 import configs
+    cfg, u0 = configs.fp32_256()
+    P = core.Problem(n, a=tuple(cfg.a), nu0=cfg.nu0, nu_amp=cfg.nu_amp, nu_omega=cfg.nu_omega)
+    t0 = time.perf_counter()
+    P.rk4(u0, 0, cfg.dt_fine, n_steps)
+    dt = time.perf_counter() - t0
+    return n ** 3 * n_steps / dt / 1e9, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import build as obuild
+    obuild.build()
+    for _ in range(args.warmup):
+        oracle_sample(1)
+    vals, total = [], 0.0
+    for _ in range(args.steps):
+        v, dt = oracle_sample(1)
+        vals.append(v)
+        total += dt
+    value = statistics.median(vals)
+    sample = "1 RK4 step of one 256^3 field per step (FP64 C oracle, 1 thread)"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "fp32_256 Parareal (oracle: fine RK4 steps of the same field)",
+                       "n": 256, "n_slices": 32},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------- GPU leg
+
+def run(args):
+    import numpy as np
+    import torch
+
+    rank, world, dist = dist_init(args.gpus)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    barrier(dist)
+    from paper_1409_8563_gb300 import configs, native
+
+    cfg, u0 = configs.fp32_256(seed=rank)
+    n, N = cfg.n, cfg.n_slices
+    P = n ** 3
+    nf = round(cfg.T / N / cfg.dt_fine)
+    stream = torch.cuda.Stream()
+    ctx = native.Parareal(cfg, stream=stream)
+    u0_dev = torch.from_numpy(u0).to("cuda")
+    u0_host = torch.from_numpy(u0).pin_memory()
+    out_host = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
+
+    # serial fine reference u_fine(T) on the same GPU (also the time to beat)
+    ctx.set_problem(u0_dev)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.serial_fine(None, as_reference=True)          # warm-up of the serial path
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        ctx.serial_fine(None, as_reference=True)
+        ev1.record(stream)
+    ev1.synchronize()
+    serial_ms = ev0.elapsed_time(ev1)
+
+    def solve():
+        ctx.set_problem(u0_dev)
+        return ctx.iterate(N, TOL, native.STOP_DEFECT)
+
+    ks = []
+    for _ in range(args.warmup):
+        k, h = solve()
+        ks.append(k)
+    torch.cuda.synchronize()
+    barrier(dist)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = ctx.launch_count()
+    ctx.profile(True)
+    updates = 0
+    hists = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier(dist)
+        for i in range(args.steps):
+            starts[i].record(stream)
+            k, h = solve()
+            ends[i].record(stream)
+            hists.append(h)
+            updates += sum((N - j) for j in range(k)) * P * nf
+        torch.cuda.synchronize()
+        barrier(dist)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    fine_ms, fine_launches, fine_bytes = ctx.profile_read()
+    ctx.profile(False)
+    launches = ctx.launch_count() - launches0
+    total_ms = max_over_ranks(dist, sum(step_ms))
+    updates = sum_over_ranks(dist, updates)
+    value = updates / (total_ms / 1000.0) / 1e9
+
+    # end to end through the C ABI with host buffers: H2D of u0 and D2H of
+    # the final slice inside every timed step
+    e2e_ms = []
+    for i in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.set_problem(u0_host.numpy())
+        k, _ = ctx.iterate(N, TOL, native.STOP_DEFECT)
+        ctx.get_slice(N, out_host.numpy())
+        e2e_ms.append(1000 * (time.perf_counter() - t0))
+    e2e_upd = updates / args.steps
+    e2e_value = e2e_upd / (statistics.mean(e2e_ms) / 1000.0) / 1e9
+
+    peak, peak_kind = peaks()
+    avg_launch_ms = fine_ms / max(fine_launches, 1)
+    bytes_per_launch = fine_bytes / max(fine_launches, 1)
+    achieved = bytes_per_launch / (avg_launch_ms / 1000.0) / 1e9
+    traffic = ncu_traffic()
+    k_star = max(len(h) for h in hists)
+    final_defect = float(hists[-1][-1, 2])
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import build as obuild
+        obuild.build()
+        v, dt = oracle_sample(args.cpu_steps)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_steps} FP64 RK4 steps of one 256^3 field (C oracle, 1 thread, "
+                         f"{dt:.1f} s)"}
+
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "precision": "FP32 stencil; FP64 correction, norms and nu(t)",
+        "data": "synthetic",
+        "config": {"workload": "fp32_256: Parareal to d^k <= 1e-6, 256^3, N=32, dt_F=1/8192, "
+                               "coarse RK4 on 32^3 at 1/256, k^-2 field to k=32",
+                   "n": n, "n_slices": N, "fine_steps_per_slice": nf,
+                   "l2": "inputs larger than L2 (2.1 GB per field set)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "time_to_1e-6_ms": total_ms / args.steps,
+        "serial_fine_ms": serial_ms,
+        "parareal_over_serial": (total_ms / args.steps) / serial_ms,
+        "k_star": k_star, "final_defect": final_defect,
+        "roofline": {"kernel": KERNEL, "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "avg_launch_ms": avg_launch_ms, "timed_launches": fine_launches,
+                     "kernel_glups": bytes_per_launch / 8.0 / (avg_launch_ms / 1000.0) / 1e9},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": statistics.mean(e2e_ms),
+                "h2d_bytes_per_step": int(u0.nbytes), "d2h_bytes_per_step": int(out_host.numel() * 4)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,193 @@
+/*
+ * parareal.h -- C ABI of the GB300 Parareal library for the periodic 3-D
+ * advection-diffusion problem u_t + a.grad u = nu(t) Lap u (Sec. 3,
+ * Eq. adv_diff_eq of Arteaga, Ruprecht & Krause, arXiv:1409.8563).
+ *
+ * Method (Sec. 2.2, Eq. parareal):
+ *     U^{k+1}[n+1] = G(U^{k+1}[n]) + F(U^k[n]) - G(U^k[n]),  n = 0..N_p-1,
+ * with F = classical RK4 with step dt_fine (Sec. 2.3) on the fine grid, and G
+ * = RK4 with step dt_coarse on the grid coarsened by coarse_factor (box
+ * restriction, trilinear prolongation; the spatial coarsening of Sec. 2.2.2),
+ * a periodic integer shift, or a learned convolution net.  The spatial
+ * operator is the 7-point Laplacian of Sec. 2.3 times nu(t) plus centred
+ * first differences for advection.  All time slices of an iteration advance
+ * concurrently on one GPU.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * - Fields are n^3 arrays, x fastest: index (z*n + y)*n + x, point x_i = i/n.
+ * - A pointer argument is a device pointer when the accompanying `mem`
+ *   argument is PARAREAL_MEM_DEVICE and a host pointer when it is
+ *   PARAREAL_MEM_HOST.  Host buffers are copied with cudaMemcpyAsync on the
+ *   context stream and the call synchronises that stream before returning.
+ * - Caller-supplied buffers are borrowed for the duration of the call only;
+ *   the context owns all of its device workspace and frees it in
+ *   parareal_destroy.
+ * - Device work is ordered on the context stream (the stream passed to
+ *   parareal_create; NULL = the legacy default stream).  Calls that return
+ *   host scalars synchronise that stream.
+ * - Every call returns a parareal_status.  Failures never throw across the
+ *   ABI; the message of the last failure is available from
+ *   parareal_last_error.  After PARAREAL_E_CUDA the context must be
+ *   destroyed; after any other error it stays usable.
+ * - Not thread-safe: one context must not be used by two host threads at
+ *   once.  Distinct contexts are independent.
+ */
+#ifndef PARAREAL_H
+#define PARAREAL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct parareal_ctx parareal_ctx;
+
+typedef enum {
+    PARAREAL_OK = 0,
+    PARAREAL_W_MARGINAL = 1,   /* created; the stability pre-check found growth > 1 per
+                                  step, accepted because allow_unstable was set */
+    PARAREAL_E_INVALID = -1,   /* bad argument or configuration */
+    PARAREAL_E_UNSTABLE = -2,  /* stability pre-check failed (see parareal_stability) */
+    PARAREAL_E_NOMEM = -3,     /* device allocation failed */
+    PARAREAL_E_CUDA = -4,      /* CUDA runtime error; destroy the context */
+    PARAREAL_E_DIVERGED = -5,  /* NaN or Inf detected in the iterate */
+    PARAREAL_E_TIMEOUT = -6,   /* a bounded device-side wait gave up */
+    PARAREAL_E_STATE = -7      /* call out of order (e.g. iterate before set_problem) */
+} parareal_status;
+
+enum { PARAREAL_F32 = 0, PARAREAL_F64 = 1 };
+enum { PARAREAL_MEM_DEVICE = 0, PARAREAL_MEM_HOST = 1 };
+
+/* Stage times of nu(t) inside an RK4 step starting at t:
+ * STAGE  = classical non-autonomous RK4 (t, t+dt/2, t+dt/2, t+dt);
+ * FROZEN = nu(t) for all four stages. */
+enum { PARAREAL_NU_STAGE = 0, PARAREAL_NU_FROZEN = 1 };
+
+/* Coarse propagator kinds. */
+enum {
+    PARAREAL_COARSE_STENCIL = 0,  /* RK4 on the (coarsened) grid */
+    PARAREAL_COARSE_LEARNED = 1,  /* shift + convolution net (parareal_set_coarse_model) */
+    PARAREAL_COARSE_SHIFT = 2     /* periodic integer shift only (the net set to zero) */
+};
+
+/* Stopping rules for parareal_iterate. */
+enum {
+    PARAREAL_STOP_DIFF = 0,    /* max_n ||U^{k+1}[n]-U^k[n]||_inf / ||U^{k+1}[n]||_inf <= tol */
+    PARAREAL_STOP_DEFECT = 1,  /* d^k of Eq. (defect) against parareal_set_reference <= tol */
+    PARAREAL_STOP_NONE = 2     /* run exactly k_max iterations */
+};
+
+/* Residual kinds for parareal_residual. */
+enum {
+    PARAREAL_RES_DIFF_INF = 0, /* per slice ||U^{k+1}[n]-U^k[n]||_inf / ||U^{k+1}[n]||_inf, last iteration */
+    PARAREAL_RES_DIFF_L2 = 1,  /* same with the 2-norm */
+    PARAREAL_RES_FINE = 2,     /* per slice ||F(U[n-1]) - U[n]||_inf / ||U[n]||_inf (runs one fine sweep) */
+    PARAREAL_RES_DEFECT = 3,   /* ||U[N_p]-ref||_inf/||ref||_inf at index N_p; others 0 */
+    PARAREAL_RES_FINE_L2 = 4   /* as PARAREAL_RES_FINE with the 2-norm */
+};
+
+typedef struct {
+    int n;                 /* grid edge; n^3 points; multiple of 4, 8..1024 */
+    int n_slices;          /* N_p >= 1 */
+    double T;              /* final time; slices are [n T/N_p, (n+1) T/N_p] */
+    double dt_fine;        /* delta t; T/(N_p dt_fine) must be an integer N_f */
+    double dt_coarse;      /* Delta t; T/(N_p dt_coarse) must be an integer N_c */
+    int coarse_factor;     /* r >= 1 dividing n, n/r >= 4: G runs on (n/r)^3 */
+    double a[3];           /* advection velocity (x, y, z) */
+    double nu0, nu_amp, nu_omega;  /* nu(t) = nu0 (1 + nu_amp sin(nu_omega t)) */
+    int fine_dtype;        /* PARAREAL_F32 or PARAREAL_F64: arithmetic of F and G */
+    int nu_mode;           /* PARAREAL_NU_STAGE or PARAREAL_NU_FROZEN */
+    int coarse_kind;       /* PARAREAL_COARSE_* */
+    int allow_unstable;    /* nonzero: stability pre-check failures become a warning */
+} parareal_config;
+
+/* Validate cfg, run the stability pre-check, allocate all device workspace
+ * and return a context bound to `cuda_stream` (a cudaStream_t; NULL = default
+ * stream) on the current device.  On failure *out is NULL. */
+parareal_status parareal_create(const parareal_config *cfg, void *cuda_stream,
+                                parareal_ctx **out);
+
+/* Stability pre-check without allocation: the largest per-step amplification
+ * max |R(dt lambda(k))| over all Fourier modes k of the fine and coarse grids
+ * and over nu in [nu0(1-|amp|), nu0(1+|amp|)], where R is the RK4 polynomial
+ * and lambda the symbol of the 7-point/centred operator.  growth[0] = fine,
+ * growth[1] = coarse (stencil G only, else 0).  Returns E_UNSTABLE when either
+ * exceeds 1 + 1e-12 (the per-step value is still written). */
+parareal_status parareal_stability(const parareal_config *cfg, double *growth2);
+
+/* Set u0 = U[0] (Algorithm 1, "Data: initial condition") and reset the
+ * iteration: every U^0[n] is produced by the initial serial coarse run on the
+ * next parareal_iterate.  u0: n^3 values of `dtype`; `mem` says where. */
+parareal_status parareal_set_problem(parareal_ctx *ctx, const void *u0, int dtype, int mem);
+
+/* Fine propagator on a batch of slices (the concurrent F evaluations of
+ * Sec. 2.2): Fv[n+1] = F(U[n]) for n in [first_slice, first_slice + count).
+ * All slices run in the same launches. */
+parareal_status parareal_fine_sweep(parareal_ctx *ctx, int first_slice, int count);
+
+/* Coarse propagator.  chain = 1: the serial start-up run (Algorithm 1,
+ * initialisation) U[n+1] = G(U[n]) and Gold[n+1] = G(U[n]) for n = first..first+count-1
+ * in order.  chain = 0: Gold[n+1] = G(U[n]) for every slice in the range, U unchanged. */
+parareal_status parareal_coarse_sweep(parareal_ctx *ctx, int first_slice, int count, int chain);
+
+/* Run Parareal iterations (Algorithm 1 loop body for all slices): fine sweep
+ * over the slices not yet exact, then the serial coarse sweep with the
+ * correction U^{k+1}[n+1] = F(U^k[n]) + (G(U^{k+1}[n]) - G(U^k[n])) and the
+ * defect norms, until the stopping rule holds or k_max iterations ran.  The
+ * first call after set_problem first runs the coarse start-up chain.
+ * k_done (may be NULL) receives the number of iterations run by this call;
+ * hist (may be NULL) receives 4 doubles per iteration: {max_n diff_inf,
+ * max_n diff_l2, defect (or -1 without a reference), elapsed ms}. */
+parareal_status parareal_iterate(parareal_ctx *ctx, int k_max, double tol, int stop_rule,
+                                 int *k_done, double *hist);
+
+/* Per-slice residuals of the current iterate; per_slice_out receives
+ * n_slices + 1 doubles (index 0 = u0, always 0). */
+parareal_status parareal_residual(parareal_ctx *ctx, int kind, double *per_slice_out);
+
+/* Reference solution u_fine(T) for the defect d^k (Eq. defect). */
+parareal_status parareal_set_reference(parareal_ctx *ctx, const void *ref, int dtype, int mem);
+
+/* Serial fine run of all slices (Eq. fine applied for n = 0..N_p-1) from u0;
+ * writes u_fine(T) to dst (n^3 values of dtype, `mem` says where) and, when
+ * `as_reference` is nonzero, also stores it as the defect reference. */
+parareal_status parareal_serial_fine(parareal_ctx *ctx, void *dst, int dtype, int mem,
+                                     int as_reference);
+
+/* Copy U[slice] (0..n_slices) out of / into the context, converting to/from dtype. */
+parareal_status parareal_get_slice(parareal_ctx *ctx, int slice, void *dst, int dtype, int mem);
+parareal_status parareal_set_slice(parareal_ctx *ctx, int slice, const void *src, int dtype, int mem);
+
+/* Apply F or G of time slice first_slice+i to count caller fields in place
+ * of the context's iterate: dst[i] = P(src[i]) where src and dst hold count
+ * consecutive n^3 fields of `dtype` in device memory.  which = 0: F, 1: G. */
+parareal_status parareal_propagate(parareal_ctx *ctx, int which, const void *src, void *dst,
+                                   int dtype, int first_slice, int count);
+
+/* Kernel timing.  While enabled, the context records a pair of CUDA events
+ * (on its stream) around every launch of the fine propagator's step kernel
+ * and accumulates them; parareal_profile_read synchronises the stream and
+ * returns the summed device time (ms), the number of timed launches and the
+ * algorithmic bytes they moved (one read and one write of every field per
+ * RK4 step), then clears the accumulators.  Enabling also clears them. */
+parareal_status parareal_profile(parareal_ctx *ctx, int enable);
+parareal_status parareal_profile_read(parareal_ctx *ctx, double *fine_ms, long long *fine_launches,
+                                      double *fine_bytes);
+
+/* Number of kernel launches this context issued so far (for reporting). */
+long long parareal_launch_count(const parareal_ctx *ctx);
+
+/* Message of the last failure of this context ("" if none); with ctx NULL,
+ * the last failure of parareal_create on this thread. */
+const char *parareal_last_error(const parareal_ctx *ctx);
+
+/* Free all device workspace.  NULL is accepted. */
+void parareal_destroy(parareal_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PARAREAL_H */

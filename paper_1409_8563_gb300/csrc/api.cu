@@ -1,0 +1,835 @@
+// api.cu -- the C ABI of include/parareal.h: context, workspace, and the
+// orchestration of Parareal (Eq. parareal, Algorithm 1) on one GPU.
+//
+// HBM layout of a context (P = n^3, Pc = (n/r)^3, N = n_slices, T = the
+// arithmetic type of F and G):
+//   U      (N+1) x P  FP64   the iterate U^k[0..N]
+//   Fv     (N+1) x P  T      Fv[n+1] = F(U^k[n]) of the current iteration
+//   Gold   N pointers to P (r = 1, FP64) or Pc (r > 1, T) fields: G(U^k[n])
+//   gspare one more such field: the newest G output, swapped into Gold
+//   wA,wB  N x P      T      ping-pong state of the batched fine sweep
+//   wC     N x P      T      (staged RK4 path only) RK4 accumulator
+//   cA..cD            T      coarse-propagator state
+//   wS     P          T      state of the serial fine run
+//   tmpd   2P         FP64   host/device conversions, propagate() scratch
+//   ref    P          FP64   u_fine(T) for the defect d^k (optional)
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace pr;
+
+namespace {
+thread_local std::string g_create_error;
+enum { PATH_FUSED = 0, PATH_STAGED = 1 };
+}
+
+struct parareal_ctx {
+    parareal_config cfg{};
+    cudaStream_t st = nullptr;
+    int dev = 0;
+    int n = 0, N = 0, r = 1, nc = 0;
+    long long P = 0, Pc = 0, Nf = 0, Nc = 0;
+    bool f64 = false;
+    size_t esz = 4;
+
+    double *U = nullptr;
+    void *Fv = nullptr;
+    std::vector<void *> gold;     // gold[s] = G(U^k[s-1]) for s = 1..N (index 0 unused)
+    void *gspare = nullptr;
+    void *wA = nullptr, *wB = nullptr, *wC = nullptr;
+    void *cA = nullptr, *cB = nullptr, *cC = nullptr, *cD = nullptr;
+    double *tmpd = nullptr;       // 2P doubles: conversions and propagate() scratch
+    void *wS = nullptr;           // P of T: state of the serial fine run
+    double *ref = nullptr;
+    double *partials = nullptr;
+    int nblk = 0;
+    double *slice_norms = nullptr;  // (N+1) x 5 on device
+    double *h_norms = nullptr;      // pinned copy
+
+    bool has_problem = false, started = false, has_ref = false;
+    int k_total = 0;
+    std::vector<double> diff_inf, diff_l2;   // last iteration, per slice
+
+    int fine_path = PATH_FUSED, fine_tx = 64, fine_ty = 16, fine_zc = 0;
+    int coarse_path = PATH_FUSED, coarse_tx = 32, coarse_ty = 8, coarse_zc = 0;
+
+    std::string err;
+    long long launches = 0;
+
+    // kernel timing (parareal_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;   // pairs: start, stop
+    size_t ev_used = 0;
+    double prof_bytes = 0.0;
+    long long prof_launches = 0;
+};
+
+// ------------------------------------------------------------ utilities
+
+static parareal_status fail(parareal_ctx *c, parareal_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(c, PARAREAL_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define LK(call)                                                                              \
+    do {                                                                                      \
+        ++c->launches;                                                                        \
+        CK(call);                                                                             \
+    } while (0)
+
+static bool is_integer_ratio(double a, double b, long long *q)
+{
+    if (!(b > 0.0) || !(a > 0.0)) return false;
+    const double x = a / b;
+    const long long r = std::llround(x);
+    if (r < 1 || std::fabs(x - (double)r) > 1e-9 * x) return false;
+    *q = r;
+    return true;
+}
+
+// Largest |R(dt lambda)| over Fourier modes and sampled nu, R the RK4
+// polynomial, lambda the symbol of the 7-point / centred operator.
+static double rk4_growth(int n, double dt, const double a[3], double nu_lo, double nu_hi)
+{
+    const int stride = n <= 64 ? 1 : n / 64;
+    std::vector<double> L1(n), S1(n);
+    for (int k = 0; k < n; ++k) {
+        const double th = 2.0 * M_PI * k / n;
+        L1[k] = (2.0 * std::cos(th) - 2.0) * n * (double)n;
+        S1[k] = std::sin(th) * n;
+    }
+    double g = 0.0;
+    const double nus[5] = {nu_lo, 0.75 * nu_lo + 0.25 * nu_hi, 0.5 * (nu_lo + nu_hi),
+                           0.25 * nu_lo + 0.75 * nu_hi, nu_hi};
+    auto scan = [&](int kx, int ky, int kz) {
+        const double L = L1[kx] + L1[ky] + L1[kz];
+        const double D = -(a[0] * S1[kx] + a[1] * S1[ky] + a[2] * S1[kz]);
+        for (double nu : nus) {
+            const std::complex<double> z(dt * nu * L, dt * D);
+            const std::complex<double> R = 1.0 + z + z * z / 2.0 + z * z * z / 6.0 + z * z * z * z / 24.0;
+            g = std::max(g, std::abs(R));
+        }
+    };
+    for (int kz = 0; kz < n; kz += stride)
+        for (int ky = 0; ky < n; ky += stride)
+            for (int kx = 0; kx < n; kx += stride) scan(kx, ky, kz);
+    scan(n / 2, n / 2, n / 2);
+    return g;
+}
+
+static parareal_status validate(const parareal_config *cfg, long long *Nf, long long *Nc,
+                                std::string *msg)
+{
+    if (!cfg) { *msg = "null config"; return PARAREAL_E_INVALID; }
+    if (cfg->n < 8 || cfg->n > 1024 || cfg->n % 4) { *msg = "n must be a multiple of 4 in 8..1024"; return PARAREAL_E_INVALID; }
+    if (cfg->n_slices < 1 || cfg->n_slices > 4096) { *msg = "n_slices must be in 1..4096"; return PARAREAL_E_INVALID; }
+    if (!(cfg->T > 0.0)) { *msg = "T must be positive"; return PARAREAL_E_INVALID; }
+    if (cfg->coarse_factor < 1 || cfg->n % cfg->coarse_factor || cfg->n / cfg->coarse_factor < 4) {
+        *msg = "coarse_factor must divide n and leave a coarse edge of at least 4";
+        return PARAREAL_E_INVALID;
+    }
+    if (cfg->fine_dtype != PARAREAL_F32 && cfg->fine_dtype != PARAREAL_F64) { *msg = "fine_dtype"; return PARAREAL_E_INVALID; }
+    if (cfg->nu_mode != PARAREAL_NU_STAGE && cfg->nu_mode != PARAREAL_NU_FROZEN) { *msg = "nu_mode"; return PARAREAL_E_INVALID; }
+    if (cfg->coarse_kind < PARAREAL_COARSE_STENCIL || cfg->coarse_kind > PARAREAL_COARSE_SHIFT) { *msg = "coarse_kind"; return PARAREAL_E_INVALID; }
+    if (cfg->coarse_kind != PARAREAL_COARSE_STENCIL) { *msg = "this build supports the stencil coarse propagator only"; return PARAREAL_E_INVALID; }
+    const double slice = cfg->T / cfg->n_slices;
+    if (!is_integer_ratio(slice, cfg->dt_fine, Nf)) { *msg = "T/(n_slices dt_fine) must be an integer"; return PARAREAL_E_INVALID; }
+    if (!is_integer_ratio(slice, cfg->dt_coarse, Nc)) { *msg = "T/(n_slices dt_coarse) must be an integer"; return PARAREAL_E_INVALID; }
+    if (!(cfg->nu0 > 0.0) || !(std::fabs(cfg->nu_amp) < 1.0)) { *msg = "need nu0 > 0 and |nu_amp| < 1"; return PARAREAL_E_INVALID; }
+    return PARAREAL_OK;
+}
+
+extern "C" parareal_status parareal_stability(const parareal_config *cfg, double *growth2)
+{
+    long long Nf, Nc;
+    std::string msg;
+    parareal_status s = validate(cfg, &Nf, &Nc, &msg);
+    if (s != PARAREAL_OK) return fail(nullptr, s, msg);
+    const double lo = cfg->nu0 * (1.0 - std::fabs(cfg->nu_amp));
+    const double hi = cfg->nu0 * (1.0 + std::fabs(cfg->nu_amp));
+    const double gf = rk4_growth(cfg->n, cfg->dt_fine, cfg->a, lo, hi);
+    const double gc = cfg->coarse_kind == PARAREAL_COARSE_STENCIL
+                          ? rk4_growth(cfg->n / cfg->coarse_factor, cfg->dt_coarse, cfg->a, lo, hi)
+                          : 0.0;
+    if (growth2) { growth2[0] = gf; growth2[1] = gc; }
+    if (gf > 1.0 + 1e-12 || gc > 1.0 + 1e-12) {
+        g_create_error = "stability pre-check: per-step growth fine " + std::to_string(gf) +
+                         ", coarse " + std::to_string(gc);
+        return PARAREAL_E_UNSTABLE;
+    }
+    return PARAREAL_OK;
+}
+
+// Pick tile shapes: fused path for FP32 (bandwidth-bound; halo recompute is
+// cheap), staged path for FP64 (FP64 throughput-bound; no recompute).
+static void default_tiles(int dtype, int n, int count, int *path, int *tx, int *ty, int *zc)
+{
+    *path = dtype == PARAREAL_F64 ? PATH_STAGED : PATH_FUSED;
+    const int cand[][2] = {{64, 16}, {32, 16}, {32, 8}, {16, 16}};
+    const int candd[][2] = {{32, 8}, {16, 16}, {16, 8}};
+    *tx = *ty = 0;
+    if (dtype == PARAREAL_F32) {
+        for (auto &t : cand)
+            if (rk4_fused_supported(dtype, n, t[0], t[1])) { *tx = t[0]; *ty = t[1]; break; }
+    } else {
+        for (auto &t : candd)
+            if (rk4_fused_supported(dtype, n, t[0], t[1])) { *tx = t[0]; *ty = t[1]; break; }
+    }
+    if (*tx == 0) { *path = PATH_STAGED; *tx = 16; *ty = 8; }
+    // z chunk: whole columns unless the launch would leave SMs idle
+    int z = n;
+    while (z > 16 && (long long)count * (n / *tx) * (n / *ty) * ((n + z - 1) / z) < 2 * 152) z /= 2;
+    *zc = z;
+}
+
+static bool tile_override(const char *var, int dtype, int n, int *path, int *tx, int *ty, int *zc)
+{
+    const char *e = std::getenv(var);
+    if (!e || !*e) return true;
+    int p, x, y, z;
+    if (std::sscanf(e, "%d,%d,%d,%d", &p, &x, &y, &z) != 4) return false;
+    if (p != PATH_FUSED && p != PATH_STAGED) return false;
+    if (p == PATH_FUSED && (!rk4_fused_supported(dtype, n, x, y) || z < 1)) return false;
+    *path = p; *tx = x; *ty = y; *zc = z;
+    return true;
+}
+
+// Record the start event of one timed launch (its stop event is the next in the pool).
+static parareal_status prof_begin(parareal_ctx *c)
+{
+    while (c->ev_pool.size() < c->ev_used + 2) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        c->ev_pool.push_back(e);
+    }
+    CK(cudaEventRecord(c->ev_pool[c->ev_used], c->st));
+    c->ev_used += 2;
+    return PARAREAL_OK;
+}
+
+template <typename T>
+static parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, int first_slice,
+                                 int count, long long nsteps, double dt, int path, int tx, int ty,
+                                 int zc, T *ws1, T *ws2, T *ws3)
+{
+    StepArgs a{};
+    a.n = m;
+    a.P = (long long)m * m * m;
+    a.count = count;
+    a.first_slice = first_slice;
+    a.steps_per_slice = nsteps;
+    a.dt = dt;
+    for (int d = 0; d < 3; ++d) a.a[d] = c->cfg.a[d];
+    a.nu0 = c->cfg.nu0;
+    a.nu_amp = c->cfg.nu_amp;
+    a.nu_omega = c->cfg.nu_omega;
+    a.frozen = c->cfg.nu_mode == PARAREAL_NU_FROZEN;
+    if (path == PATH_FUSED) {
+        const T *src = in;
+        const bool timed = c->prof && m == c->n;
+        for (long long j = 0; j < nsteps; ++j) {
+            T *dst = (j == nsteps - 1) ? out : ((j & 1) ? ws2 : ws1);
+            a.j = j;
+            if (timed) {
+                parareal_status ps = prof_begin(c);
+                if (ps != PARAREAL_OK) return ps;
+            }
+            LK((launch_rk4_fused<T>(a, src, dst, tx, ty, zc, c->st)));
+            if (timed) {
+                CK(cudaEventRecord(c->ev_pool[c->ev_used - 1], c->st));
+                c->prof_bytes += 2.0 * (double)count * (double)a.P * sizeof(T);
+                c->prof_launches++;
+            }
+            src = dst;
+        }
+    } else {
+        if (in != out)
+            CK(cudaMemcpyAsync(out, in, (size_t)count * a.P * sizeof(T), cudaMemcpyDeviceToDevice, c->st));
+        for (long long j = 0; j < nsteps; ++j) {
+            a.j = j;
+            LK(launch_rk4_stage<T>(a, 1, out, out, ws1, ws3, c->st));
+            LK(launch_rk4_stage<T>(a, 2, ws1, out, ws2, ws3, c->st));
+            LK(launch_rk4_stage<T>(a, 3, ws2, out, ws1, ws3, c->st));
+            LK(launch_rk4_stage<T>(a, 4, ws1, out, nullptr, ws3, c->st));
+        }
+    }
+    return PARAREAL_OK;
+}
+
+// ------------------------------------------------------------ propagators
+
+// Fv[s+1] = F(U[s]) for s in [first, first+count).
+template <typename T>
+static parareal_status fine_sweep_t(parareal_ctx *c, int first, int count)
+{
+    const long long P = c->P;
+    T *Fv = static_cast<T *>(c->Fv) + (long long)(first + 1) * P;
+    const T *in;
+    if (std::is_same<T, float>::value) {
+        LK(launch_convert_f64_to_f32(c->U + (long long)first * P, reinterpret_cast<float *>(c->wC ? c->wC : c->wA),
+                                     (long long)count * P, c->st));
+        in = static_cast<const T *>(c->wC ? c->wC : c->wA);
+    } else {
+        in = reinterpret_cast<const T *>(c->U + (long long)first * P);
+    }
+    // the fused path must not read and write the same buffer
+    T *ws1 = static_cast<T *>(c->wA), *ws2 = static_cast<T *>(c->wB), *ws3 = static_cast<T *>(c->wC);
+    if (c->fine_path == PATH_FUSED && in == ws1) std::swap(ws1, ws3);
+    return rk4_batch<T>(c, c->n, in, Fv, first, count, c->Nf, c->cfg.dt_fine, c->fine_path,
+                        c->fine_tx, c->fine_ty, c->fine_zc, ws1, ws2, ws3);
+}
+
+// G(U_in) for slice s into `out` (Pc T fields when r > 1, P doubles when r = 1).
+template <typename T>
+static parareal_status coarse_apply_t(parareal_ctx *c, const double *Uin, int s, void *out)
+{
+    T *cA = static_cast<T *>(c->cA), *cB = static_cast<T *>(c->cB), *cC = static_cast<T *>(c->cC),
+      *cD = static_cast<T *>(c->cD);
+    if (c->r > 1) {
+        LK(launch_restrict<T>(Uin, c->n, c->r, cA, c->st));
+        return rk4_batch<T>(c, c->nc, cA, static_cast<T *>(out), s, 1, c->Nc, c->cfg.dt_coarse,
+                            c->coarse_path, c->coarse_tx, c->coarse_ty, c->coarse_zc, cB, cC, cD);
+    }
+    if (std::is_same<T, float>::value) {
+        LK(launch_convert_f64_to_f32(Uin, reinterpret_cast<float *>(cA), c->P, c->st));
+        parareal_status ps = rk4_batch<T>(c, c->n, cA, cB, s, 1, c->Nc, c->cfg.dt_coarse,
+                                          c->coarse_path, c->coarse_tx, c->coarse_ty, c->coarse_zc,
+                                          cC, cD, cA);
+        if (ps != PARAREAL_OK) return ps;
+        LK(launch_convert_f32_to_f64(reinterpret_cast<const float *>(cB), static_cast<double *>(out), c->P, c->st));
+        return PARAREAL_OK;
+    }
+    return rk4_batch<T>(c, c->n, reinterpret_cast<const T *>(Uin), static_cast<T *>(out), s, 1,
+                        c->Nc, c->cfg.dt_coarse, c->coarse_path, c->coarse_tx, c->coarse_ty,
+                        c->coarse_zc, cB, cC, cD);
+}
+
+// U[s+1] <- Fv[s+1] + (gnew - gold) with norms into slice_norms[s+1].
+// Fv / gold may be null (read as zero).
+template <typename T>
+static parareal_status correct_t(parareal_ctx *c, int s, const void *gnew, const void *gold,
+                                 bool with_fine)
+{
+    const T *Fv = with_fine ? static_cast<const T *>(c->Fv) + (long long)(s + 1) * c->P : nullptr;
+    double *U = c->U + (long long)(s + 1) * c->P;
+    if (c->r > 1) {
+        LK((launch_correct<T, T>(Fv, static_cast<const T *>(gnew), static_cast<const T *>(gold), U,
+                                 c->n, c->r, c->partials, c->nblk, c->st)));
+    } else {
+        LK((launch_correct<T, double>(Fv, static_cast<const double *>(gnew),
+                                      static_cast<const double *>(gold), U, c->n, 1, c->partials,
+                                      c->nblk, c->st)));
+    }
+    LK(launch_reduce_partials(c->partials, c->nblk, c->slice_norms + 5ll * (s + 1), c->st));
+    return PARAREAL_OK;
+}
+
+#define DISPATCH(c, fn, ...) ((c)->f64 ? fn<double>(c, __VA_ARGS__) : fn<float>(c, __VA_ARGS__))
+
+// Serial coarse start-up (Algorithm 1, initialisation) for slices first..first+count-1.
+static parareal_status coarse_chain(parareal_ctx *c, int first, int count, bool chain)
+{
+    for (int s = first; s < first + count; ++s) {
+        parareal_status ps = DISPATCH(c, coarse_apply_t, c->U + (long long)s * c->P, s, c->gspare);
+        if (ps != PARAREAL_OK) return ps;
+        if (chain) {
+            ps = DISPATCH(c, correct_t, s, c->gspare, nullptr, false);
+            if (ps != PARAREAL_OK) return ps;
+        }
+        std::swap(c->gspare, c->gold[s + 1]);
+    }
+    return PARAREAL_OK;
+}
+
+static parareal_status read_norms(parareal_ctx *c, int from, int to)
+{
+    CK(cudaMemcpyAsync(c->h_norms, c->slice_norms, sizeof(double) * 5 * (c->N + 1),
+                       cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (int s = 0; s <= c->N; ++s) {
+        if (s < from || s > to) { c->diff_inf[s] = 0.0; c->diff_l2[s] = 0.0; continue; }
+        const double *q = c->h_norms + 5 * s;
+        if (q[4] != 0.0) return fail(c, PARAREAL_E_DIVERGED, "non-finite value in slice " + std::to_string(s));
+        c->diff_inf[s] = q[1] > 0 ? q[0] / q[1] : q[0];
+        c->diff_l2[s] = q[3] > 0 ? std::sqrt(q[2] / q[3]) : std::sqrt(q[2]);
+    }
+    return PARAREAL_OK;
+}
+
+static parareal_status defect(parareal_ctx *c, double *d)
+{
+    LK(launch_diff_norms<double>(c->U + (long long)c->N * c->P, c->ref, c->P, c->partials, c->nblk, c->st));
+    LK(launch_reduce_partials(c->partials, c->nblk, c->slice_norms, c->st));
+    double h[5];
+    CK(cudaMemcpyAsync(h, c->slice_norms, sizeof h, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (h[4] != 0.0) return fail(c, PARAREAL_E_DIVERGED, "non-finite value in the last slice");
+    *d = h[1] > 0 ? h[0] / h[1] : h[0];
+    return PARAREAL_OK;
+}
+
+// ------------------------------------------------------------------- ABI
+
+extern "C" parareal_status parareal_create(const parareal_config *cfg, void *stream,
+                                           parareal_ctx **out)
+{
+    if (!out) return fail(nullptr, PARAREAL_E_INVALID, "null out");
+    *out = nullptr;
+    long long Nf, Nc;
+    std::string msg;
+    parareal_status s = validate(cfg, &Nf, &Nc, &msg);
+    if (s != PARAREAL_OK) return fail(nullptr, s, msg);
+    double growth[2];
+    parareal_status warn = PARAREAL_OK;
+    if (parareal_stability(cfg, growth) == PARAREAL_E_UNSTABLE) {
+        if (!cfg->allow_unstable) return PARAREAL_E_UNSTABLE;
+        warn = PARAREAL_W_MARGINAL;
+    }
+    parareal_ctx *c = new parareal_ctx();
+    c->cfg = *cfg;
+    c->st = static_cast<cudaStream_t>(stream);
+    c->n = cfg->n;
+    c->N = cfg->n_slices;
+    c->r = cfg->coarse_factor;
+    c->nc = c->n / c->r;
+    c->P = (long long)c->n * c->n * c->n;
+    c->Pc = (long long)c->nc * c->nc * c->nc;
+    c->Nf = Nf;
+    c->Nc = Nc;
+    c->f64 = cfg->fine_dtype == PARAREAL_F64;
+    c->esz = c->f64 ? 8 : 4;
+    c->diff_inf.assign(c->N + 1, 0.0);
+    c->diff_l2.assign(c->N + 1, 0.0);
+    default_tiles(cfg->fine_dtype, c->n, c->N, &c->fine_path, &c->fine_tx, &c->fine_ty, &c->fine_zc);
+    default_tiles(cfg->fine_dtype, c->nc, 1, &c->coarse_path, &c->coarse_tx, &c->coarse_ty, &c->coarse_zc);
+    // explicit launch shapes ("path,tile_x,tile_y,zchunk"), e.g. from the autotuner
+    if (!tile_override("PARAREAL_FINE_TILE", cfg->fine_dtype, c->n, &c->fine_path, &c->fine_tx,
+                       &c->fine_ty, &c->fine_zc) ||
+        !tile_override("PARAREAL_COARSE_TILE", cfg->fine_dtype, c->nc, &c->coarse_path,
+                       &c->coarse_tx, &c->coarse_ty, &c->coarse_zc)) {
+        delete c;
+        return fail(nullptr, PARAREAL_E_INVALID, "unsupported launch shape override");
+    }
+
+    auto alloc = [&](void **p, size_t bytes) -> bool {
+        if (cudaMalloc(p, bytes) != cudaSuccess) { cudaGetLastError(); *p = nullptr; return false; }
+        return true;
+    };
+    const size_t e = c->esz;
+    const size_t P = (size_t)c->P, Pc = (size_t)c->Pc, N = (size_t)c->N;
+    const size_t gbytes = c->r > 1 ? Pc * e : P * sizeof(double);
+    bool ok = cudaGetDevice(&c->dev) == cudaSuccess;
+    ok = ok && alloc((void **)&c->U, (N + 1) * P * sizeof(double));
+    ok = ok && alloc(&c->Fv, (N + 1) * P * e);
+    c->gold.assign(N + 1, nullptr);
+    for (size_t i = 1; ok && i <= N; ++i) ok = alloc(&c->gold[i], gbytes);
+    ok = ok && alloc(&c->gspare, gbytes);
+    ok = ok && alloc(&c->wA, N * P * e) && alloc(&c->wB, N * P * e) && alloc(&c->wC, N * P * e);
+    const size_t cbytes = (c->r > 1 ? Pc : P) * e;
+    ok = ok && alloc(&c->cA, cbytes) && alloc(&c->cB, cbytes) && alloc(&c->cC, cbytes) && alloc(&c->cD, cbytes);
+    ok = ok && alloc((void **)&c->tmpd, 2 * P * sizeof(double));
+    ok = ok && alloc(&c->wS, P * e);
+    c->nblk = correct_blocks(c->P);
+    ok = ok && alloc((void **)&c->partials, 5 * sizeof(double) * (size_t)c->nblk);
+    ok = ok && alloc((void **)&c->slice_norms, 5 * sizeof(double) * (N + 1));
+    ok = ok && cudaMallocHost((void **)&c->h_norms, 5 * sizeof(double) * (N + 1)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        parareal_destroy(c);
+        return fail(nullptr, PARAREAL_E_NOMEM, "device allocation failed");
+    }
+    if (cudaMemsetAsync(c->slice_norms, 0, 5 * sizeof(double) * (N + 1), c->st) != cudaSuccess) {
+        parareal_destroy(c);
+        return fail(nullptr, PARAREAL_E_CUDA, "memset failed");
+    }
+    *out = c;
+    return warn;
+}
+
+extern "C" void parareal_destroy(parareal_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    void *ptrs[] = {c->U, c->Fv, c->gspare, c->wA, c->wB, c->wC, c->cA, c->cB, c->cC, c->cD,
+                    c->tmpd, c->wS, c->ref, c->partials, c->slice_norms};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (void *p : c->gold)
+        if (p) cudaFree(p);
+    if (c->h_norms) cudaFreeHost(c->h_norms);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+extern "C" const char *parareal_last_error(const parareal_ctx *c)
+{
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" long long parareal_launch_count(const parareal_ctx *c) { return c ? c->launches : 0; }
+
+extern "C" parareal_status parareal_profile(parareal_ctx *c, int enable)
+{
+    if (!c) return PARAREAL_E_INVALID;
+    CK(cudaStreamSynchronize(c->st));
+    c->prof = enable != 0;
+    c->ev_used = 0;
+    c->prof_bytes = 0.0;
+    c->prof_launches = 0;
+    return PARAREAL_OK;
+}
+
+extern "C" parareal_status parareal_profile_read(parareal_ctx *c, double *ms, long long *launches,
+                                                 double *bytes)
+{
+    if (!c) return PARAREAL_E_INVALID;
+    CK(cudaStreamSynchronize(c->st));
+    double total = 0.0;
+    for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, c->ev_pool[i], c->ev_pool[i + 1]));
+        total += t;
+    }
+    if (ms) *ms = total;
+    if (launches) *launches = c->prof_launches;
+    if (bytes) *bytes = c->prof_bytes;
+    c->ev_used = 0;
+    c->prof_bytes = 0.0;
+    c->prof_launches = 0;
+    return PARAREAL_OK;
+}
+
+// Copy n^3 values of `dtype` at src (host or device) into the FP64 field dst.
+static parareal_status load_field(parareal_ctx *c, double *dst, const void *src, int dtype, int mem)
+{
+    if (!src) return fail(c, PARAREAL_E_INVALID, "null field pointer");
+    if (dtype != PARAREAL_F32 && dtype != PARAREAL_F64) return fail(c, PARAREAL_E_INVALID, "dtype");
+    if (mem != PARAREAL_MEM_DEVICE && mem != PARAREAL_MEM_HOST) return fail(c, PARAREAL_E_INVALID, "mem");
+    const size_t bytes = (size_t)c->P * (dtype == PARAREAL_F64 ? 8 : 4);
+    const cudaMemcpyKind kind = mem == PARAREAL_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (dtype == PARAREAL_F64) {
+        CK(cudaMemcpyAsync(dst, src, bytes, kind, c->st));
+    } else {
+        float *stage = reinterpret_cast<float *>(c->tmpd) + c->P;   // upper half of tmpd
+        CK(cudaMemcpyAsync(stage, src, bytes, kind, c->st));
+        LK(launch_convert_f32_to_f64(stage, dst, c->P, c->st));
+    }
+    if (mem == PARAREAL_MEM_HOST) CK(cudaStreamSynchronize(c->st));
+    return PARAREAL_OK;
+}
+
+static parareal_status store_field(parareal_ctx *c, void *dst, const double *src, int dtype, int mem)
+{
+    if (!dst) return fail(c, PARAREAL_E_INVALID, "null field pointer");
+    if (dtype != PARAREAL_F32 && dtype != PARAREAL_F64) return fail(c, PARAREAL_E_INVALID, "dtype");
+    if (mem != PARAREAL_MEM_DEVICE && mem != PARAREAL_MEM_HOST) return fail(c, PARAREAL_E_INVALID, "mem");
+    const cudaMemcpyKind kind = mem == PARAREAL_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (dtype == PARAREAL_F64) {
+        CK(cudaMemcpyAsync(dst, src, (size_t)c->P * 8, kind, c->st));
+    } else {
+        float *stage = reinterpret_cast<float *>(c->tmpd) + c->P;
+        LK(launch_convert_f64_to_f32(src, stage, c->P, c->st));
+        CK(cudaMemcpyAsync(dst, stage, (size_t)c->P * 4, kind, c->st));
+    }
+    if (mem == PARAREAL_MEM_HOST) CK(cudaStreamSynchronize(c->st));
+    return PARAREAL_OK;
+}
+
+extern "C" parareal_status parareal_set_problem(parareal_ctx *c, const void *u0, int dtype, int mem)
+{
+    if (!c) return PARAREAL_E_INVALID;
+    parareal_status s = load_field(c, c->U, u0, dtype, mem);
+    if (s != PARAREAL_OK) return s;
+    c->has_problem = true;
+    c->started = false;
+    c->k_total = 0;
+    std::fill(c->diff_inf.begin(), c->diff_inf.end(), 0.0);
+    std::fill(c->diff_l2.begin(), c->diff_l2.end(), 0.0);
+    return PARAREAL_OK;
+}
+
+extern "C" parareal_status parareal_set_reference(parareal_ctx *c, const void *ref, int dtype, int mem)
+{
+    if (!c) return PARAREAL_E_INVALID;
+    if (!c->ref && cudaMalloc((void **)&c->ref, (size_t)c->P * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->ref = nullptr;
+        return fail(c, PARAREAL_E_NOMEM, "reference allocation failed");
+    }
+    parareal_status s = load_field(c, c->ref, ref, dtype, mem);
+    if (s == PARAREAL_OK) c->has_ref = true;
+    return s;
+}
+
+extern "C" parareal_status parareal_get_slice(parareal_ctx *c, int slice, void *dst, int dtype, int mem)
+{
+    if (!c) return PARAREAL_E_INVALID;
+    if (slice < 0 || slice > c->N) return fail(c, PARAREAL_E_INVALID, "slice out of range");
+    return store_field(c, dst, c->U + (long long)slice * c->P, dtype, mem);
+}
+
+extern "C" parareal_status parareal_set_slice(parareal_ctx *c, int slice, const void *src, int dtype, int mem)
+{
+    if (!c) return PARAREAL_E_INVALID;
+    if (slice < 0 || slice > c->N) return fail(c, PARAREAL_E_INVALID, "slice out of range");
+    return load_field(c, c->U + (long long)slice * c->P, src, dtype, mem);
+}
+
+extern "C" parareal_status parareal_fine_sweep(parareal_ctx *c, int first, int count)
+{
+    if (!c) return PARAREAL_E_INVALID;
+    if (first < 0 || count < 0 || first + count > c->N) return fail(c, PARAREAL_E_INVALID, "slice range");
+    if (count == 0) return PARAREAL_OK;
+    return DISPATCH(c, fine_sweep_t, first, count);
+}
+
+extern "C" parareal_status parareal_coarse_sweep(parareal_ctx *c, int first, int count, int chain)
+{
+    if (!c) return PARAREAL_E_INVALID;
+    if (first < 0 || count < 0 || first + count > c->N) return fail(c, PARAREAL_E_INVALID, "slice range");
+    return coarse_chain(c, first, count, chain != 0);
+}
+
+extern "C" parareal_status parareal_iterate(parareal_ctx *c, int k_max, double tol, int stop_rule,
+                                            int *k_done, double *hist)
+{
+    if (!c) return PARAREAL_E_INVALID;
+    if (k_done) *k_done = 0;
+    if (!c->has_problem) return fail(c, PARAREAL_E_STATE, "set_problem first");
+    if (k_max < 0) return fail(c, PARAREAL_E_INVALID, "k_max < 0");
+    if (stop_rule == PARAREAL_STOP_DEFECT && !c->has_ref) return fail(c, PARAREAL_E_STATE, "no reference set");
+    if (stop_rule < 0 || stop_rule > 2) return fail(c, PARAREAL_E_INVALID, "stop_rule");
+    parareal_status s;
+    if (!c->started) {
+        s = coarse_chain(c, 0, c->N, true);
+        if (s != PARAREAL_OK) return s;
+        c->started = true;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    int done = 0;
+    for (; done < k_max && c->k_total < c->N; ++done) {
+        const int K = c->k_total;   // U[0..K] are exact
+        s = DISPATCH(c, fine_sweep_t, K, c->N - K);
+        if (s != PARAREAL_OK) return s;
+        // slice K+1: its input U[K] did not change, so G's difference is zero
+        s = DISPATCH(c, correct_t, K, c->gold[K + 1], c->gold[K + 1], true);
+        if (s != PARAREAL_OK) return s;
+        for (int n = K + 1; n < c->N; ++n) {
+            s = DISPATCH(c, coarse_apply_t, c->U + (long long)n * c->P, n, c->gspare);
+            if (s != PARAREAL_OK) return s;
+            s = DISPATCH(c, correct_t, n, c->gspare, c->gold[n + 1], true);
+            if (s != PARAREAL_OK) return s;
+            std::swap(c->gspare, c->gold[n + 1]);
+        }
+        s = read_norms(c, K + 1, c->N);
+        if (s != PARAREAL_OK) return s;
+        c->k_total++;
+        double dmax = 0.0, l2max = 0.0;
+        for (int n = 0; n <= c->N; ++n) {
+            dmax = std::max(dmax, c->diff_inf[n]);
+            l2max = std::max(l2max, c->diff_l2[n]);
+        }
+        double d = -1.0;
+        if (c->has_ref) {
+            s = defect(c, &d);
+            if (s != PARAREAL_OK) return s;
+        }
+        if (hist) {
+            hist[4 * done + 0] = dmax;
+            hist[4 * done + 1] = l2max;
+            hist[4 * done + 2] = d;
+            hist[4 * done + 3] =
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        }
+        if (stop_rule == PARAREAL_STOP_DIFF && dmax <= tol) { ++done; break; }
+        if (stop_rule == PARAREAL_STOP_DEFECT && d <= tol) { ++done; break; }
+    }
+    if (k_done) *k_done = done;
+    return PARAREAL_OK;
+}
+
+extern "C" parareal_status parareal_residual(parareal_ctx *c, int kind, double *out)
+{
+    if (!c || !out) return PARAREAL_E_INVALID;
+    std::fill(out, out + c->N + 1, 0.0);
+    if (kind == PARAREAL_RES_DIFF_INF || kind == PARAREAL_RES_DIFF_L2) {
+        for (int n = 0; n <= c->N; ++n)
+            out[n] = kind == PARAREAL_RES_DIFF_INF ? c->diff_inf[n] : c->diff_l2[n];
+        return PARAREAL_OK;
+    }
+    if (!c->has_problem) return fail(c, PARAREAL_E_STATE, "set_problem first");
+    if (kind == PARAREAL_RES_DEFECT) {
+        if (!c->has_ref) return fail(c, PARAREAL_E_STATE, "no reference set");
+        return defect(c, &out[c->N]);
+    }
+    if (kind != PARAREAL_RES_FINE && kind != PARAREAL_RES_FINE_L2) return fail(c, PARAREAL_E_INVALID, "kind");
+    // ||F(U[n-1]) - U[n]||_inf / ||U[n]||_inf: one fine sweep into Fv, then
+    // the norm of Fv[n] - U[n] per slice.
+    parareal_status s = DISPATCH(c, fine_sweep_t, 0, c->N);
+    if (s != PARAREAL_OK) return s;
+    for (int n = 1; n <= c->N; ++n) {
+        if (c->f64) {
+            LK(launch_diff_norms<double>(static_cast<const double *>(c->Fv) + (long long)n * c->P,
+                                         c->U + (long long)n * c->P, c->P, c->partials, c->nblk, c->st));
+        } else {
+            LK(launch_diff_norms<float>(static_cast<const float *>(c->Fv) + (long long)n * c->P,
+                                        c->U + (long long)n * c->P, c->P, c->partials, c->nblk, c->st));
+        }
+        LK(launch_reduce_partials(c->partials, c->nblk, c->slice_norms + 5ll * n, c->st));
+    }
+    CK(cudaMemcpyAsync(c->h_norms, c->slice_norms, sizeof(double) * 5 * (c->N + 1), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (int n = 1; n <= c->N; ++n) {
+        const double *q = c->h_norms + 5 * n;
+        if (kind == PARAREAL_RES_FINE) out[n] = q[1] > 0 ? q[0] / q[1] : q[0];
+        else out[n] = q[3] > 0 ? std::sqrt(q[2] / q[3]) : std::sqrt(q[2]);
+    }
+    return PARAREAL_OK;
+}
+
+extern "C" parareal_status parareal_serial_fine(parareal_ctx *c, void *dst, int dtype, int mem,
+                                                int as_reference)
+{
+    if (!c) return PARAREAL_E_INVALID;
+    if (!c->has_problem) return fail(c, PARAREAL_E_STATE, "set_problem first");
+    // march slice after slice in the fine arithmetic type; slice boundaries
+    // pass through Fv[1] (F's output of one slice is the next slice's input)
+    const long long P = c->P;
+    parareal_status s = PARAREAL_OK;
+    if (c->f64) {
+        double *cur = static_cast<double *>(c->wS);
+        CK(cudaMemcpyAsync(cur, c->U, P * 8, cudaMemcpyDeviceToDevice, c->st));
+        double *Fv1 = static_cast<double *>(c->Fv) + P;
+        for (int n = 0; n < c->N && s == PARAREAL_OK; ++n) {
+            s = rk4_batch<double>(c, c->n, cur, Fv1, n, 1, c->Nf, c->cfg.dt_fine, c->fine_path,
+                                  c->fine_tx, c->fine_ty, c->fine_zc, static_cast<double *>(c->wA),
+                                  static_cast<double *>(c->wB), static_cast<double *>(c->wC));
+            if (s == PARAREAL_OK) CK(cudaMemcpyAsync(cur, Fv1, P * 8, cudaMemcpyDeviceToDevice, c->st));
+        }
+        if (s != PARAREAL_OK) return s;
+        CK(cudaMemcpyAsync(c->tmpd, cur, P * 8, cudaMemcpyDeviceToDevice, c->st));
+    } else {
+        float *cur = static_cast<float *>(c->wS);
+        LK(launch_convert_f64_to_f32(c->U, cur, P, c->st));
+        float *Fv1 = static_cast<float *>(c->Fv) + P;
+        for (int n = 0; n < c->N && s == PARAREAL_OK; ++n) {
+            s = rk4_batch<float>(c, c->n, cur, Fv1, n, 1, c->Nf, c->cfg.dt_fine, c->fine_path,
+                                 c->fine_tx, c->fine_ty, c->fine_zc, static_cast<float *>(c->wA),
+                                 static_cast<float *>(c->wB), static_cast<float *>(c->wC));
+            if (s == PARAREAL_OK) CK(cudaMemcpyAsync(cur, Fv1, P * 4, cudaMemcpyDeviceToDevice, c->st));
+        }
+        if (s != PARAREAL_OK) return s;
+        LK(launch_convert_f32_to_f64(cur, c->tmpd, P, c->st));
+    }
+    if (as_reference) {
+        if (!c->ref && cudaMalloc((void **)&c->ref, (size_t)P * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            c->ref = nullptr;
+            return fail(c, PARAREAL_E_NOMEM, "reference allocation failed");
+        }
+        CK(cudaMemcpyAsync(c->ref, c->tmpd, P * 8, cudaMemcpyDeviceToDevice, c->st));
+        c->has_ref = true;
+    }
+    if (dst) {
+        // tmpd holds the result; store_field stages through tmpd's upper half
+        // only for FP32, which does not overlap the FP64 values in use.
+        if (dtype == PARAREAL_F64) {
+            CK(cudaMemcpyAsync(dst, c->tmpd, P * 8, mem == PARAREAL_MEM_HOST ? cudaMemcpyDeviceToHost
+                                                                             : cudaMemcpyDeviceToDevice, c->st));
+            if (mem == PARAREAL_MEM_HOST) CK(cudaStreamSynchronize(c->st));
+        } else {
+            float *stage = static_cast<float *>(c->wA);
+            LK(launch_convert_f64_to_f32(c->tmpd, stage, P, c->st));
+            CK(cudaMemcpyAsync(dst, stage, P * 4, mem == PARAREAL_MEM_HOST ? cudaMemcpyDeviceToHost
+                                                                          : cudaMemcpyDeviceToDevice, c->st));
+            if (mem == PARAREAL_MEM_HOST) CK(cudaStreamSynchronize(c->st));
+        }
+    }
+    return PARAREAL_OK;
+}
+
+template <typename T>
+static parareal_status propagate_t(parareal_ctx *c, int which, const void *src, void *dst,
+                                   int dtype, int first, int count)
+{
+    const long long P = c->P;
+    const size_t es = dtype == PARAREAL_F64 ? 8 : 4;
+    for (int f = 0; f < count; ++f) {
+        const char *sp = static_cast<const char *>(src) + (size_t)f * P * es;
+        char *dp = static_cast<char *>(dst) + (size_t)f * P * es;
+        double *in64 = c->tmpd;          // input as FP64
+        double *res64 = c->tmpd + P;     // result as FP64
+        if (dtype == PARAREAL_F64) {
+            CK(cudaMemcpyAsync(in64, sp, P * 8, cudaMemcpyDeviceToDevice, c->st));
+        } else {
+            LK(launch_convert_f32_to_f64(reinterpret_cast<const float *>(sp), in64, P, c->st));
+        }
+        parareal_status s;
+        if (which == 0) {
+            // input in the serial-state buffer, output in the unused Fv[0]
+            // slot, fine-sized workspaces wA..wC
+            T *tin = static_cast<T *>(c->wS), *tout = static_cast<T *>(c->Fv);
+            if (std::is_same<T, float>::value)
+                LK(launch_convert_f64_to_f32(in64, reinterpret_cast<float *>(tin), P, c->st));
+            else
+                CK(cudaMemcpyAsync(tin, in64, P * 8, cudaMemcpyDeviceToDevice, c->st));
+            s = rk4_batch<T>(c, c->n, tin, tout, first + f, 1, c->Nf, c->cfg.dt_fine, c->fine_path,
+                             c->fine_tx, c->fine_ty, c->fine_zc, static_cast<T *>(c->wA),
+                             static_cast<T *>(c->wB), static_cast<T *>(c->wC));
+            if (s != PARAREAL_OK) return s;
+            if (std::is_same<T, float>::value)
+                LK(launch_convert_f32_to_f64(reinterpret_cast<const float *>(tout), res64, P, c->st));
+            else
+                CK(cudaMemcpyAsync(res64, tout, P * 8, cudaMemcpyDeviceToDevice, c->st));
+        } else {
+            s = coarse_apply_t<T>(c, in64, first + f, c->gspare);
+            if (s != PARAREAL_OK) return s;
+            // res64 = G output on the fine grid: U-style correction with
+            // null F and null old value, written into res64
+            CK(cudaMemsetAsync(res64, 0, P * 8, c->st));
+            const T *nullT = nullptr;
+            if (c->r > 1) {
+                LK((launch_correct<T, T>(nullT, static_cast<const T *>(c->gspare), nullptr, res64,
+                                         c->n, c->r, c->partials, c->nblk, c->st)));
+            } else {
+                LK((launch_correct<T, double>(nullT, static_cast<const double *>(c->gspare), nullptr,
+                                              res64, c->n, 1, c->partials, c->nblk, c->st)));
+            }
+        }
+        if (dtype == PARAREAL_F64) {
+            CK(cudaMemcpyAsync(dp, res64, P * 8, cudaMemcpyDeviceToDevice, c->st));
+        } else {
+            LK(launch_convert_f64_to_f32(res64, reinterpret_cast<float *>(dp), P, c->st));
+        }
+    }
+    return PARAREAL_OK;
+}
+
+extern "C" parareal_status parareal_propagate(parareal_ctx *c, int which, const void *src,
+                                              void *dst, int dtype, int first, int count)
+{
+    if (!c) return PARAREAL_E_INVALID;
+    if (!src || !dst || (which != 0 && which != 1)) return fail(c, PARAREAL_E_INVALID, "arguments");
+    if (dtype != PARAREAL_F32 && dtype != PARAREAL_F64) return fail(c, PARAREAL_E_INVALID, "dtype");
+    if (first < 0 || count < 0 || first + count > c->N) return fail(c, PARAREAL_E_INVALID, "slice range");
+    return DISPATCH(c, propagate_t, which, src, dst, dtype, first, count);
+}

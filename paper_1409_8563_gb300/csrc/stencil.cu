@@ -1,0 +1,440 @@
+// stencil.cu -- RK4 time steps of the periodic advection-diffusion operator
+// A(t) y = nu(t) Lap_7 y - a . D_2 y   (7-point Laplacian of Sec. 2.3,
+// centred first differences), classical RK4 (Sec. 2.3 fine propagator):
+//
+//   d1 = dt A(t1) u,        y2 = u + d1/2
+//   d2 = dt A(t2) y2,       y3 = u + d2/2
+//   d3 = dt A(t2) y3,       y4 = u + d3
+//   d4 = dt A(t4) y4,       u' = u + (d1/6 + d2/3 + d3/3 + d4/6)
+//
+// with t1 = t, t2 = t + dt/2, t4 = t + dt (or all t when nu is frozen), t the
+// step start (s * dt for global step index s).
+//
+// Two kernels:
+//   rk4_fused_kernel  one full step per launch.  Each CTA owns a TX x TY
+//                     column of the grid plus a 4-point halo in x and y and
+//                     marches along z; the four stages are software-pipelined
+//                     along z (stage s works on plane z-s), each stage's
+//                     current plane sits in shared memory for its x/y
+//                     neighbours and its z neighbours sit in registers.  HBM
+//                     traffic: one read and one write of the field per step.
+//   rk4_stage_kernel  one stage per launch, one point per thread; no halo
+//                     recomputation, so the fewest arithmetic operations per
+//                     step (the right trade where FP64 throughput, not
+//                     bandwidth, bounds the step).
+#include <type_traits>
+
+#include "internal.cuh"
+
+namespace pr {
+
+template <typename T> struct VecT;
+template <> struct VecT<float> {
+    static constexpr int V = 4;
+    using type = float4;
+};
+template <> struct VecT<double> {
+    static constexpr int V = 2;
+    using type = double2;
+};
+
+template <typename T>
+__device__ __forceinline__ void ldv(const T *p, T (&r)[VecT<T>::V]);
+template <>
+__device__ __forceinline__ void ldv<float>(const float *p, float (&r)[4])
+{
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    r[0] = q.x; r[1] = q.y; r[2] = q.z; r[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void ldv<double>(const double *p, double (&r)[2])
+{
+    const double2 q = *reinterpret_cast<const double2 *>(p);
+    r[0] = q.x; r[1] = q.y;
+}
+template <typename T>
+__device__ __forceinline__ void ldg_v(const T *p, T (&r)[VecT<T>::V]);
+template <>
+__device__ __forceinline__ void ldg_v<float>(const float *p, float (&r)[4])
+{
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+    r[0] = q.x; r[1] = q.y; r[2] = q.z; r[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void ldg_v<double>(const double *p, double (&r)[2])
+{
+    const double2 q = __ldg(reinterpret_cast<const double2 *>(p));
+    r[0] = q.x; r[1] = q.y;
+}
+template <typename T>
+__device__ __forceinline__ void stv(T *p, const T (&r)[VecT<T>::V]);
+template <>
+__device__ __forceinline__ void stv<float>(float *p, const float (&r)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(r[0], r[1], r[2], r[3]);
+}
+template <>
+__device__ __forceinline__ void stv<double>(double *p, const double (&r)[2])
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(r[0], r[1]);
+}
+
+__device__ __forceinline__ double nu_at(const StepArgs &a, double t)
+{
+    return a.nu0 * (1.0 + a.nu_amp * sin(a.nu_omega * t));
+}
+
+// delta[i] = sum of the 7 weighted neighbours of point i of this thread's
+// vector.  c / zm / zp: this column at planes p, p-1, p+1 (registers);
+// the x and y neighbours come from the shared-memory plane Sp ([RY][RX]).
+template <typename T, int RX, int RY>
+__device__ __forceinline__ void stage_delta(T (&d)[VecT<T>::V], const T *__restrict__ Sp, int qx,
+                                            int ry, const T (&c)[VecT<T>::V],
+                                            const T (&zm)[VecT<T>::V],
+                                            const T (&zp)[VecT<T>::V], const T (&w)[7])
+{
+    constexpr int V = VecT<T>::V;
+    const int rym = ry > 0 ? ry - 1 : 0;
+    const int ryp = ry < RY - 1 ? ry + 1 : RY - 1;
+    const int xl = qx * V > 0 ? qx * V - 1 : 0;
+    const int xr = qx * V + V < RX ? qx * V + V : RX - 1;
+    T ym[V], yp[V];
+    ldv<T>(Sp + rym * RX + qx * V, ym);
+    ldv<T>(Sp + ryp * RX + qx * V, yp);
+    const T left = Sp[ry * RX + xl];
+    const T right = Sp[ry * RX + xr];
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        const T l = (i == 0) ? left : c[i - 1];
+        const T r = (i == V - 1) ? right : c[i + 1];
+        T acc = w[0] * c[i];
+        acc = fma(w[1], l, acc);
+        acc = fma(w[2], r, acc);
+        acc = fma(w[3], ym[i], acc);
+        acc = fma(w[4], yp[i], acc);
+        acc = fma(w[5], zm[i], acc);
+        acc = fma(w[6], zp[i], acc);
+        d[i] = acc;
+    }
+}
+
+template <typename T, int TX, int TY>
+struct FusedShape {
+    static constexpr int V = VecT<T>::V;
+    static constexpr int RX = TX + 8;          // region width incl. 4-point halo per side
+    static constexpr int RY = TY + 8;
+    static constexpr int QX = RX / V;          // vectors per region row
+    static constexpr int NT = QX * RY;         // threads per CTA
+    static constexpr size_t SMEM = 2ull * 4 * RX * RY * sizeof(T);  // double-buffered stage planes
+};
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(FusedShape<T, TX, TY>::NT, 1)
+rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int tiles_x,
+                 int tiles_y, int zchunk, int nzc)
+{
+    using S = FusedShape<T, TX, TY>;
+    constexpr int V = S::V, RX = S::RX, RY = S::RY, QX = S::QX;
+    constexpr int PL = RX * RY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *planes = reinterpret_cast<T *>(smem_raw);   // [2][4][RY][RX]
+    __shared__ T s_w[3][7];                        // stage 1, stages 2-3, stage 4
+
+    const int tid = threadIdx.x;
+    const int qx = tid % QX;
+    const int ry = tid / QX;
+    int b = blockIdx.x;
+    const int zc = b % nzc; b /= nzc;
+    const int tx = b % tiles_x; b /= tiles_x;
+    const int ty = b % tiles_y; b /= tiles_y;
+    const int f = b;
+    const int n = a.n;
+
+    if (tid < 3) {
+        const long long s = (long long)(a.first_slice + f) * a.steps_per_slice + a.j;
+        const double t = (double)s * a.dt;
+        const double ts = a.frozen ? t : (tid == 0 ? t : (tid == 1 ? t + 0.5 * a.dt : t + a.dt));
+        double w[7];
+        stage_weights(nu_at(a, ts), a.dt, n, a.a, w);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) s_w[tid][k] = (T)w[k];
+    }
+    __syncthreads();
+    T w1[7], w2[7], w4[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        w1[k] = s_w[0][k];
+        w2[k] = s_w[1][k];
+        w4[k] = s_w[2][k];
+    }
+
+    const int gx = ((tx * TX - 4 + qx * V) % n + n) % n;
+    const int gy = ((ty * TY - 4 + ry) % n + n) % n;
+    const long long plane = (long long)n * n;
+    const T *src = in + (long long)f * a.P + (long long)gy * n + gx;
+    T *dst = out + (long long)f * a.P + (long long)gy * n + gx;
+
+    // stage s is needed on rows [s, RY-s) and elements [s, RX-s) of the region
+    auto active = [&](int s) {
+        return ry >= s && ry < RY - s && (qx + 1) * V > s && qx * V < RX - s;
+    };
+    const bool act1 = active(1), act2 = active(2), act3 = active(3), act4 = active(4);
+    const bool owner = ry >= 4 && ry < 4 + TY && qx * V >= 4 && qx * V < 4 + TX;
+
+    const int z_lo = zc * zchunk;
+    const int z_hi = min(z_lo + zchunk, n);
+
+    // register windows (index 0 = newest plane)
+    T U[4][V] = {}, Y2[2][V] = {}, Y3[2][V] = {}, Y4[2][V] = {}, A[3][V] = {};
+    constexpr T c6 = (T)(1.0 / 6.0), c3 = (T)(1.0 / 3.0), hf = (T)0.5;
+
+    int cur = 0;
+    for (int zi = z_lo - 4; zi < z_hi + 4; ++zi) {
+        const int zw = ((zi % n) + n) % n;
+        T un[V];
+        ldg_v<T>(src + (long long)zw * plane, un);
+        const T *Sc = planes + cur * 4 * PL;
+        T *Sn = planes + (cur ^ 1) * 4 * PL;
+        T d[V];
+        T y2n[V] = {}, y3n[V] = {}, y4n[V] = {}, accn[V] = {};
+        // stage 1 at plane zi-1
+        if (act1) {
+            stage_delta<T, RX, RY>(d, Sc, qx, ry, U[0], U[1], un, w1);
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                y2n[i] = fma(hf, d[i], U[0][i]);
+                accn[i] = c6 * d[i];
+            }
+        }
+        // stage 2 at plane zi-2
+        if (act2) {
+            stage_delta<T, RX, RY>(d, Sc + PL, qx, ry, Y2[0], Y2[1], y2n, w2);
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                y3n[i] = fma(hf, d[i], U[1][i]);
+                A[0][i] = fma(c3, d[i], A[0][i]);
+            }
+        }
+        // stage 3 at plane zi-3
+        if (act3) {
+            stage_delta<T, RX, RY>(d, Sc + 2 * PL, qx, ry, Y3[0], Y3[1], y3n, w2);
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                y4n[i] = U[2][i] + d[i];
+                A[1][i] = fma(c3, d[i], A[1][i]);
+            }
+        }
+        // stage 4 at plane zi-4: the finished step
+        if (act4) {
+            stage_delta<T, RX, RY>(d, Sc + 3 * PL, qx, ry, Y4[0], Y4[1], y4n, w4);
+            const int zo = zi - 4;
+            if (owner && zo >= z_lo) {
+                T o[V];
+#pragma unroll
+                for (int i = 0; i < V; ++i) o[i] = U[3][i] + fma(c6, d[i], A[2][i]);
+                stv<T>(dst + (long long)zo * plane, o);
+            }
+        }
+        stv<T>(Sn + ry * RX + qx * V, un);
+        stv<T>(Sn + PL + ry * RX + qx * V, y2n);
+        stv<T>(Sn + 2 * PL + ry * RX + qx * V, y3n);
+        stv<T>(Sn + 3 * PL + ry * RX + qx * V, y4n);
+        __syncthreads();
+        cur ^= 1;
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            U[3][i] = U[2][i]; U[2][i] = U[1][i]; U[1][i] = U[0][i]; U[0][i] = un[i];
+            Y2[1][i] = Y2[0][i]; Y2[0][i] = y2n[i];
+            Y3[1][i] = Y3[0][i]; Y3[0][i] = y3n[i];
+            Y4[1][i] = Y4[0][i]; Y4[0][i] = y4n[i];
+            A[2][i] = A[1][i]; A[1][i] = A[0][i]; A[0][i] = accn[i];
+        }
+    }
+}
+
+template <typename T, int TX, int TY>
+static cudaError_t launch_fused_shape(const StepArgs &a, const T *in, T *out, int zchunk,
+                                      cudaStream_t st)
+{
+    using S = FusedShape<T, TX, TY>;
+    static bool configured = false;   // per template instance, per process
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(rk4_fused_kernel<T, TX, TY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)S::SMEM);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int tiles_x = a.n / TX, tiles_y = a.n / TY;
+    const int nzc = (a.n + zchunk - 1) / zchunk;
+    const long long blocks = (long long)a.count * tiles_x * tiles_y * nzc;
+    rk4_fused_kernel<T, TX, TY><<<(unsigned)blocks, S::NT, S::SMEM, st>>>(a, in, out, tiles_x,
+                                                                         tiles_y, zchunk, nzc);
+    return cudaGetLastError();
+}
+
+// Tile shapes compiled for the fused kernel.
+#define PR_FUSED_SHAPES(X) \
+    X(float, 64, 16)       \
+    X(float, 64, 8)        \
+    X(float, 32, 16)       \
+    X(float, 32, 8)        \
+    X(float, 16, 16)       \
+    X(double, 32, 8)       \
+    X(double, 16, 16)      \
+    X(double, 16, 8)
+
+bool rk4_fused_supported(int dtype, int n, int tile_x, int tile_y)
+{
+    if (n % tile_x || n % tile_y) return false;
+#define PR_SUP(T, TX, TY)                                                                   \
+    if ((dtype == PARAREAL_F64) == (sizeof(T) == 8) && tile_x == TX && tile_y == TY) return true;
+    PR_FUSED_SHAPES(PR_SUP)
+#undef PR_SUP
+    return false;
+}
+
+template <typename T>
+cudaError_t launch_rk4_fused(const StepArgs &a, const T *in, T *out, int tile_x, int tile_y,
+                             int zchunk, cudaStream_t st)
+{
+    if (zchunk <= 0 || a.n % tile_x || a.n % tile_y) return cudaErrorInvalidValue;
+#define PR_DISPATCH(TT, TX, TY)                                                             \
+    if constexpr (std::is_same<T, TT>::value)                                                \
+        if (tile_x == TX && tile_y == TY) return launch_fused_shape<TT, TX, TY>(a, in, out, zchunk, st);
+    PR_FUSED_SHAPES(PR_DISPATCH)
+#undef PR_DISPATCH
+    return cudaErrorInvalidValue;
+}
+template cudaError_t launch_rk4_fused<float>(const StepArgs &, const float *, float *, int, int,
+                                             int, cudaStream_t);
+template cudaError_t launch_rk4_fused<double>(const StepArgs &, const double *, double *, int,
+                                              int, int, cudaStream_t);
+
+// ------------------------------------------------------------ staged RK4
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+rk4_stage_kernel(StepArgs a, int stage, const T *__restrict__ ysrc, T *__restrict__ u,
+                 T *__restrict__ ydst, T *__restrict__ acc)
+{
+    __shared__ T s_w[7];
+    const int f = blockIdx.y;
+    if (threadIdx.x == 0) {
+        const long long s = (long long)(a.first_slice + f) * a.steps_per_slice + a.j;
+        const double t = (double)s * a.dt;
+        const double c = (stage == 1 || a.frozen) ? 0.0 : (stage == 4 ? 1.0 : 0.5);
+        double w[7];
+        stage_weights(nu_at(a, t + c * a.dt), a.dt, a.n, a.a, w);
+        for (int k = 0; k < 7; ++k) s_w[k] = (T)w[k];
+    }
+    __syncthreads();
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.P) return;
+    const int n = a.n;
+    const int x = (int)(p % n), y = (int)((p / n) % n), z = (int)(p / ((long long)n * n));
+    const long long off = (long long)f * a.P;
+    const T *Y = ysrc + off;
+    const int xm = x ? x - 1 : n - 1, xp = x + 1 < n ? x + 1 : 0;
+    const int ym = y ? y - 1 : n - 1, yp = y + 1 < n ? y + 1 : 0;
+    const int zm = z ? z - 1 : n - 1, zp = z + 1 < n ? z + 1 : 0;
+    const long long row = (long long)z * n * n + (long long)y * n;
+    T d = s_w[0] * Y[row + x];
+    d = fma(s_w[1], Y[row + xm], d);
+    d = fma(s_w[2], Y[row + xp], d);
+    d = fma(s_w[3], Y[(long long)z * n * n + (long long)ym * n + x], d);
+    d = fma(s_w[4], Y[(long long)z * n * n + (long long)yp * n + x], d);
+    d = fma(s_w[5], Y[(long long)zm * n * n + (long long)y * n + x], d);
+    d = fma(s_w[6], Y[(long long)zp * n * n + (long long)y * n + x], d);
+    const long long q = off + p;
+    const T uq = u[q];
+    if (stage == 1) {
+        ydst[q] = fma((T)0.5, d, uq);
+        acc[q] = d * (T)(1.0 / 6.0);
+    } else if (stage == 2) {
+        ydst[q] = fma((T)0.5, d, uq);
+        acc[q] = fma((T)(1.0 / 3.0), d, acc[q]);
+    } else if (stage == 3) {
+        ydst[q] = uq + d;
+        acc[q] = fma((T)(1.0 / 3.0), d, acc[q]);
+    } else {
+        u[q] = uq + fma((T)(1.0 / 6.0), d, acc[q]);
+    }
+}
+
+template <typename T>
+cudaError_t launch_rk4_stage(const StepArgs &a, int stage, const T *ysrc, T *u, T *ydst, T *acc,
+                             cudaStream_t st)
+{
+    const unsigned bx = (unsigned)((a.P + 255) / 256);
+    dim3 grid(bx, (unsigned)a.count);
+    rk4_stage_kernel<T><<<grid, 256, 0, st>>>(a, stage, ysrc, u, ydst, acc);
+    return cudaGetLastError();
+}
+template cudaError_t launch_rk4_stage<float>(const StepArgs &, int, const float *, float *,
+                                             float *, float *, cudaStream_t);
+template cudaError_t launch_rk4_stage<double>(const StepArgs &, int, const double *, double *,
+                                              double *, double *, cudaStream_t);
+
+// ------------------------------------------------- conversion, restriction
+
+__global__ void convert_d2f_kernel(const double *__restrict__ s, float *__restrict__ d, long long N)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x)
+        d[i] = (float)s[i];
+}
+__global__ void convert_f2d_kernel(const float *__restrict__ s, double *__restrict__ d, long long N)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x)
+        d[i] = (double)s[i];
+}
+
+static unsigned grid_for(long long N)
+{
+    long long b = (N + 255) / 256;
+    return (unsigned)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+cudaError_t launch_convert_f64_to_f32(const double *src, float *dst, long long N, cudaStream_t st)
+{
+    convert_d2f_kernel<<<grid_for(N), 256, 0, st>>>(src, dst, N);
+    return cudaGetLastError();
+}
+cudaError_t launch_convert_f32_to_f64(const float *src, double *dst, long long N, cudaStream_t st)
+{
+    convert_f2d_kernel<<<grid_for(N), 256, 0, st>>>(src, dst, N);
+    return cudaGetLastError();
+}
+
+// Box average over the r^3 fine points I*r..I*r+r-1 of each coarse cell.
+template <typename T>
+__global__ void restrict_kernel(const double *__restrict__ fine, int n, int r, T *__restrict__ coarse)
+{
+    const int nc = n / r;
+    const long long Pc = (long long)nc * nc * nc;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < Pc;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int I = (int)(q % nc), J = (int)((q / nc) % nc), K = (int)(q / ((long long)nc * nc));
+        double s = 0.0;
+        for (int dk = 0; dk < r; ++dk)
+            for (int dj = 0; dj < r; ++dj) {
+                const double *row = fine + ((long long)(K * r + dk) * n + (J * r + dj)) * n + I * r;
+                for (int di = 0; di < r; ++di) s += row[di];
+            }
+        coarse[q] = (T)(s / ((double)r * r * r));
+    }
+}
+
+template <typename T>
+cudaError_t launch_restrict(const double *fine, int n, int r, T *coarse, cudaStream_t st)
+{
+    const long long Pc = (long long)(n / r) * (n / r) * (n / r);
+    restrict_kernel<T><<<grid_for(Pc), 256, 0, st>>>(fine, n, r, coarse);
+    return cudaGetLastError();
+}
+template cudaError_t launch_restrict<float>(const double *, int, int, float *, cudaStream_t);
+template cudaError_t launch_restrict<double>(const double *, int, int, double *, cudaStream_t);
+
+}  // namespace pr

@@ -1,0 +1,220 @@
+"""Thin ctypes binding of the C ABI in include/parareal.h.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Field arguments may be CUDA torch tensors (passed as device
+pointers) or numpy arrays (passed as host pointers; the library copies them).
+Loading fails loudly when libparareal.so is missing: there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libparareal.so")
+
+OK, W_MARGINAL = 0, 1
+E_INVALID, E_UNSTABLE, E_NOMEM, E_CUDA, E_DIVERGED, E_TIMEOUT, E_STATE = -1, -2, -3, -4, -5, -6, -7
+F32, F64 = 0, 1
+MEM_DEVICE, MEM_HOST = 0, 1
+NU_STAGE, NU_FROZEN = 0, 1
+COARSE_STENCIL, COARSE_LEARNED, COARSE_SHIFT = 0, 1, 2
+STOP_DIFF, STOP_DEFECT, STOP_NONE = 0, 1, 2
+RES_DIFF_INF, RES_DIFF_L2, RES_FINE, RES_DEFECT, RES_FINE_L2 = 0, 1, 2, 3, 4
+
+_STATUS = {0: "OK", 1: "W_MARGINAL", -1: "E_INVALID", -2: "E_UNSTABLE", -3: "E_NOMEM",
+           -4: "E_CUDA", -5: "E_DIVERGED", -6: "E_TIMEOUT", -7: "E_STATE"}
+
+
+class PararealError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    """Mirror of parareal_config."""
+    _fields_ = [("n", ctypes.c_int), ("n_slices", ctypes.c_int), ("T", ctypes.c_double),
+                ("dt_fine", ctypes.c_double), ("dt_coarse", ctypes.c_double),
+                ("coarse_factor", ctypes.c_int), ("a", ctypes.c_double * 3),
+                ("nu0", ctypes.c_double), ("nu_amp", ctypes.c_double),
+                ("nu_omega", ctypes.c_double), ("fine_dtype", ctypes.c_int),
+                ("nu_mode", ctypes.c_int), ("coarse_kind", ctypes.c_int),
+                ("allow_unstable", ctypes.c_int)]
+
+    @classmethod
+    def make(cls, n, n_slices, T, dt_fine, dt_coarse, coarse_factor=1, a=(1.0, 1.0, 1.0),
+             nu0=0.01, nu_amp=0.5, nu_omega=2 * np.pi, fine_dtype=F32, nu_mode=NU_STAGE,
+             coarse_kind=COARSE_STENCIL, allow_unstable=0):
+        return cls(int(n), int(n_slices), float(T), float(dt_fine), float(dt_coarse),
+                   int(coarse_factor), (ctypes.c_double * 3)(*a), float(nu0), float(nu_amp),
+                   float(nu_omega), int(fine_dtype), int(nu_mode), int(coarse_kind),
+                   int(allow_unstable))
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_vp, _cp, _i, _d, _dp, _ip = (ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int, ctypes.c_double,
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int))
+SIGNATURES = {
+    "parareal_create": (_i, [ctypes.POINTER(Config), _vp, ctypes.POINTER(_vp)]),
+    "parareal_stability": (_i, [ctypes.POINTER(Config), _dp]),
+    "parareal_set_problem": (_i, [_vp, _vp, _i, _i]),
+    "parareal_fine_sweep": (_i, [_vp, _i, _i]),
+    "parareal_coarse_sweep": (_i, [_vp, _i, _i, _i]),
+    "parareal_iterate": (_i, [_vp, _i, _d, _i, _ip, _dp]),
+    "parareal_residual": (_i, [_vp, _i, _dp]),
+    "parareal_set_reference": (_i, [_vp, _vp, _i, _i]),
+    "parareal_serial_fine": (_i, [_vp, _vp, _i, _i, _i]),
+    "parareal_get_slice": (_i, [_vp, _i, _vp, _i, _i]),
+    "parareal_set_slice": (_i, [_vp, _i, _vp, _i, _i]),
+    "parareal_propagate": (_i, [_vp, _i, _vp, _vp, _i, _i, _i]),
+    "parareal_profile": (_i, [_vp, _i]),
+    "parareal_profile_read": (_i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]),
+    "parareal_launch_count": (ctypes.c_longlong, [_vp]),
+    "parareal_last_error": (_cp, [_vp]),
+    "parareal_destroy": (None, [_vp]),
+}
+
+
+def lib():
+    """Open libparareal.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() (no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _field(x):
+    """(pointer, dtype code, mem code, keepalive) for a torch tensor or numpy array."""
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("numpy field must be C-contiguous")
+        code = {np.dtype(np.float32): F32, np.dtype(np.float64): F64}[x.dtype]
+        return ctypes.c_void_p(x.ctypes.data), code, MEM_HOST, x
+    import torch
+    if not isinstance(x, torch.Tensor):
+        raise TypeError("field must be a numpy array or a torch tensor")
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    code = {torch.float32: F32, torch.float64: F64}[x.dtype]
+    mem = MEM_DEVICE if x.is_cuda else MEM_HOST
+    return ctypes.c_void_p(x.data_ptr()), code, mem, x
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def stability(cfg):
+    g = (ctypes.c_double * 2)()
+    st = lib().parareal_stability(ctypes.byref(cfg), g)
+    return st, (g[0], g[1])
+
+
+class Parareal:
+    """One context of the C library (parareal_create ... parareal_destroy)."""
+
+    def __init__(self, cfg, stream=None):
+        self.cfg = cfg
+        h = ctypes.c_void_p()
+        st = lib().parareal_create(ctypes.byref(cfg), _stream_ptr(stream), ctypes.byref(h))
+        if st < 0:
+            raise PararealError(st, lib().parareal_last_error(None).decode())
+        self.status = st
+        self._h = h
+
+    def _check(self, st):
+        if st < 0:
+            raise PararealError(st, lib().parareal_last_error(self._h).decode())
+        return st
+
+    def set_problem(self, u0):
+        p, code, mem, _k = _field(u0)
+        return self._check(lib().parareal_set_problem(self._h, p, code, mem))
+
+    def set_reference(self, ref):
+        p, code, mem, _k = _field(ref)
+        return self._check(lib().parareal_set_reference(self._h, p, code, mem))
+
+    def fine_sweep(self, first, count):
+        return self._check(lib().parareal_fine_sweep(self._h, first, count))
+
+    def coarse_sweep(self, first, count, chain=1):
+        return self._check(lib().parareal_coarse_sweep(self._h, first, count, chain))
+
+    def iterate(self, k_max, tol=0.0, stop_rule=STOP_NONE):
+        k = ctypes.c_int()
+        hist = (ctypes.c_double * (4 * max(k_max, 1)))()
+        self._check(lib().parareal_iterate(self._h, k_max, tol, stop_rule, ctypes.byref(k), hist))
+        h = np.array(hist[:4 * k.value]).reshape(k.value, 4)
+        return k.value, h
+
+    def residual(self, kind):
+        out = (ctypes.c_double * (self.cfg.n_slices + 1))()
+        self._check(lib().parareal_residual(self._h, kind, out))
+        return np.array(out[:])
+
+    def serial_fine(self, dst=None, as_reference=True):
+        if dst is None:
+            self._check(lib().parareal_serial_fine(self._h, None, F64, MEM_DEVICE, int(as_reference)))
+            return None
+        p, code, mem, _k = _field(dst)
+        return self._check(lib().parareal_serial_fine(self._h, p, code, mem, int(as_reference)))
+
+    def get_slice(self, s, dst):
+        p, code, mem, _k = _field(dst)
+        return self._check(lib().parareal_get_slice(self._h, s, p, code, mem))
+
+    def set_slice(self, s, src):
+        p, code, mem, _k = _field(src)
+        return self._check(lib().parareal_set_slice(self._h, s, p, code, mem))
+
+    def propagate(self, which, src, dst, first, count):
+        ps, code, mem, _k1 = _field(src)
+        pd, code2, mem2, _k2 = _field(dst)
+        if code != code2 or mem != MEM_DEVICE or mem2 != MEM_DEVICE:
+            raise ValueError("propagate needs device tensors of one dtype")
+        return self._check(lib().parareal_propagate(self._h, which, ps, pd, code, first, count))
+
+    def profile(self, enable=True):
+        return self._check(lib().parareal_profile(self._h, int(enable)))
+
+    def profile_read(self):
+        """(device ms, launches, algorithmic bytes) of the timed fine-kernel launches."""
+        ms, nl, by = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+        self._check(lib().parareal_profile_read(self._h, ctypes.byref(ms), ctypes.byref(nl),
+                                                ctypes.byref(by)))
+        return ms.value, nl.value, by.value
+
+    def launch_count(self):
+        return int(lib().parareal_launch_count(self._h))
+
+    def close(self):
+        if self._h:
+            lib().parareal_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
