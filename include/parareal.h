@@ -166,6 +166,58 @@ parareal_status parareal_set_slice(parareal_ctx *ctx, int slice, const void *src
 parareal_status parareal_propagate(parareal_ctx *ctx, int which, const void *src, void *dst,
                                    int dtype, int first_slice, int count);
 
+/* Learned coarse propagator (coarse_kind PARAREAL_COARSE_LEARNED; SHIFT is
+ * the same propagator with every weight zero):
+ *     G(u, t_n) = S(u) + Net([S(u), nu(t_n)/nu0])
+ * on the grid n / coarse_factor (box restriction before, trilinear
+ * prolongation after, when coarse_factor > 1).  S shifts periodically by
+ * round(a_d * (T/N_p) * m) cells per axis, the transport of one slice.  Net:
+ * 3x3x3 periodic convolutions 2 -> 16 -> 16 -> 16 -> 1 with GELU after the
+ * first three; BF16 weights and activations, FP32 accumulation.  There is no
+ * counterpart in the paper, whose G is a stencil (Algorithm 2).
+ *
+ * The model is PARAREAL_MODEL_PARAMS FP32 values, in this order (tap index
+ * (dz+1)*9 + (dy+1)*3 + (dx+1)):
+ *   W1[16][2][27] b1[16] W2[16][16][27] b2[16] W3[16][16][27] b3[16] W4[1][16][27] b4[1]
+ * A new context starts with every value zero (G = S). */
+#define PARAREAL_MODEL_PARAMS 15169
+
+typedef struct {
+    int epochs;                  /* passes over the pairs */
+    int batch;                   /* pairs per Adam step (the remainder of an epoch is dropped) */
+    double lr, beta1, beta2, eps;/* Adam */
+    unsigned long long seed;     /* shuffling seed */
+} parareal_train_config;
+
+/* Copy the model in / out (w: PARAREAL_MODEL_PARAMS floats; `mem` says
+ * where).  Setting a model resets the Adam moments and restarts the iteration
+ * at the coarse start-up on the next parareal_iterate. */
+parareal_status parareal_set_coarse_model(parareal_ctx *ctx, const float *w, int mem);
+parareal_status parareal_get_coarse_model(parareal_ctx *ctx, float *w, int mem);
+
+/* Training pairs from the fine propagator: ics holds n_ics FP32 fields
+ * (device, n^3 each); for each the serial fine trajectory over all slices
+ * gives pairs (u_n, F(u_n)), n = 0..N_p-1, written at pair index ic*N_p + n
+ * of pairs_u / pairs_f (device, FP32, on the net's grid: (n/coarse_factor)^3
+ * each).  pair_slice (host, may be NULL) receives n for every pair. */
+parareal_status parareal_make_pairs(parareal_ctx *ctx, const float *ics, int n_ics, float *pairs_u,
+                                    float *pairs_f, int *pair_slice);
+
+/* Train the model on n_pairs pairs (device FP32 fields on the net's grid;
+ * pair_slice on the host gives the slice index of each pair) by Adam on the
+ * mean squared error |G(u) - F(u)|^2 over all points of a batch.  loss_hist
+ * (host, may be NULL) receives one mean loss per epoch. */
+parareal_status parareal_train_coarse(parareal_ctx *ctx, const float *pairs_u, const float *pairs_f,
+                                      const int *pair_slice, int n_pairs,
+                                      const parareal_train_config *tc, double *loss_hist);
+
+/* One forward and backward pass without an update: the mean squared error
+ * over `count` fields (device FP32, net grid) against `target`, and its
+ * gradient (device, PARAREAL_MODEL_PARAMS floats).  slices: host, count ints. */
+parareal_status parareal_coarse_model_grad(parareal_ctx *ctx, const float *u, const float *target,
+                                           const int *slices, int count, float *grad_out,
+                                           double *loss);
+
 /* Kernel timing.  While enabled, the context records a pair of CUDA events
  * (on its stream) around every launch of the fine propagator's step kernel
  * and accumulates them; parareal_profile_read synchronises the stream and

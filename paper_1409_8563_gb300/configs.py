@@ -75,12 +75,21 @@ def paper_128(omega=100.0):
     return cfg, inputs.paper_ic(128)
 
 
-def small(n=32, n_slices=4, dtype=F64, r=1, nf=32, nc=4, T=None, seed=0, ic="spectral"):
-    """A small configuration for parity tests: N slices of nf fine / nc coarse steps."""
-    T = n_slices / 8.0 if T is None else T
-    slice_len = T / n_slices
-    cfg = Config.make(n, n_slices, T, slice_len / nf, slice_len / nc, r, fine_dtype=dtype,
-                      allow_unstable=1, **NU_BASE)
+def small(n=32, n_slices=4, dtype=F64, r=1, nf=32, nc=4, seed=0, ic="spectral"):
+    """A small stable configuration for parity tests: N slices of nf fine
+    steps with dt_F = 2^-m, z = 12 nu_max n^2 dt_F <= 1.5 on the fine grid;
+    nc is raised until the coarse step obeys the same bound on the coarse grid."""
+    nu_max = NU_BASE["nu0"] * (1 + NU_BASE["nu_amp"])
+    m = max(6, math.ceil(math.log2(12.0 * nu_max * n * n / 1.5)))
+    dt_f = 2.0 ** -m
+    slice_len = nf * dt_f
+    nco = n // r
+    need = math.ceil(12.0 * nu_max * nco * nco * slice_len / 1.5 - 1e-9)
+    nc = min(max(nc, need, 1), nf)
+    while nf % nc:          # ends at nc = nf at the latest
+        nc += 1
+    cfg = Config.make(n, n_slices, n_slices * slice_len, dt_f, slice_len / nc, r,
+                      fine_dtype=dtype, **NU_BASE)
     if ic == "spectral":
         u0 = inputs.spectral_ic(n, seed=seed, kmax=max(2, n // 8))
     else:

@@ -24,77 +24,18 @@
 #include <type_traits>
 #include <vector>
 
-#include "internal.cuh"
+#include "ctx.cuh"
 
 using namespace pr;
 
-namespace {
 thread_local std::string g_create_error;
-enum { PATH_FUSED = 0, PATH_STAGED = 1 };
-}
 
-struct parareal_ctx {
-    parareal_config cfg{};
-    cudaStream_t st = nullptr;
-    int dev = 0;
-    int n = 0, N = 0, r = 1, nc = 0;
-    long long P = 0, Pc = 0, Nf = 0, Nc = 0;
-    bool f64 = false;
-    size_t esz = 4;
-
-    double *U = nullptr;
-    void *Fv = nullptr;
-    std::vector<void *> gold;     // gold[s] = G(U^k[s-1]) for s = 1..N (index 0 unused)
-    void *gspare = nullptr;
-    void *wA = nullptr, *wB = nullptr, *wC = nullptr;
-    void *cA = nullptr, *cB = nullptr, *cC = nullptr, *cD = nullptr;
-    double *tmpd = nullptr;       // 2P doubles: conversions and propagate() scratch
-    void *wS = nullptr;           // P of T: state of the serial fine run
-    double *ref = nullptr;
-    double *partials = nullptr;
-    int nblk = 0;
-    double *slice_norms = nullptr;  // (N+1) x 5 on device
-    double *h_norms = nullptr;      // pinned copy
-
-    bool has_problem = false, started = false, has_ref = false;
-    int k_total = 0;
-    std::vector<double> diff_inf, diff_l2;   // last iteration, per slice
-
-    int fine_path = PATH_FUSED, fine_tx = 64, fine_ty = 16, fine_zc = 0;
-    int coarse_path = PATH_FUSED, coarse_tx = 32, coarse_ty = 8, coarse_zc = 0;
-
-    std::string err;
-    long long launches = 0;
-
-    // kernel timing (parareal_profile)
-    bool prof = false;
-    std::vector<cudaEvent_t> ev_pool;   // pairs: start, stop
-    size_t ev_used = 0;
-    double prof_bytes = 0.0;
-    long long prof_launches = 0;
-};
-
-// ------------------------------------------------------------ utilities
-
-static parareal_status fail(parareal_ctx *c, parareal_status s, const std::string &msg)
+parareal_status fail(parareal_ctx *c, parareal_status s, const std::string &msg)
 {
     if (c) c->err = msg;
     else g_create_error = msg;
     return s;
 }
-
-#define CK(call)                                                                              \
-    do {                                                                                      \
-        cudaError_t e_ = (call);                                                              \
-        if (e_ != cudaSuccess)                                                                \
-            return fail(c, PARAREAL_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-    } while (0)
-
-#define LK(call)                                                                              \
-    do {                                                                                      \
-        ++c->launches;                                                                        \
-        CK(call);                                                                             \
-    } while (0)
 
 static bool is_integer_ratio(double a, double b, long long *q)
 {
@@ -150,7 +91,6 @@ static parareal_status validate(const parareal_config *cfg, long long *Nf, long 
     if (cfg->fine_dtype != PARAREAL_F32 && cfg->fine_dtype != PARAREAL_F64) { *msg = "fine_dtype"; return PARAREAL_E_INVALID; }
     if (cfg->nu_mode != PARAREAL_NU_STAGE && cfg->nu_mode != PARAREAL_NU_FROZEN) { *msg = "nu_mode"; return PARAREAL_E_INVALID; }
     if (cfg->coarse_kind < PARAREAL_COARSE_STENCIL || cfg->coarse_kind > PARAREAL_COARSE_SHIFT) { *msg = "coarse_kind"; return PARAREAL_E_INVALID; }
-    if (cfg->coarse_kind != PARAREAL_COARSE_STENCIL) { *msg = "this build supports the stencil coarse propagator only"; return PARAREAL_E_INVALID; }
     const double slice = cfg->T / cfg->n_slices;
     if (!is_integer_ratio(slice, cfg->dt_fine, Nf)) { *msg = "T/(n_slices dt_fine) must be an integer"; return PARAREAL_E_INVALID; }
     if (!is_integer_ratio(slice, cfg->dt_coarse, Nc)) { *msg = "T/(n_slices dt_coarse) must be an integer"; return PARAREAL_E_INVALID; }
@@ -227,15 +167,16 @@ static parareal_status prof_begin(parareal_ctx *c)
 }
 
 template <typename T>
-static parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, int first_slice,
-                                 int count, long long nsteps, double dt, int path, int tx, int ty,
-                                 int zc, T *ws1, T *ws2, T *ws3)
+parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, int first_slice, int count,
+                          long long nsteps, double dt, int path, int tx, int ty, int zc, T *ws1,
+                          T *ws2, T *ws3, int slice_stride)
 {
     StepArgs a{};
     a.n = m;
     a.P = (long long)m * m * m;
     a.count = count;
     a.first_slice = first_slice;
+    a.slice_stride = slice_stride;
     a.steps_per_slice = nsteps;
     a.dt = dt;
     for (int d = 0; d < 3; ++d) a.a[d] = c->cfg.a[d];
@@ -275,6 +216,13 @@ static parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, in
     return PARAREAL_OK;
 }
 
+template parareal_status rk4_batch<float>(parareal_ctx *, int, const float *, float *, int, int,
+                                          long long, double, int, int, int, int, float *, float *,
+                                          float *, int);
+template parareal_status rk4_batch<double>(parareal_ctx *, int, const double *, double *, int, int,
+                                           long long, double, int, int, int, int, double *,
+                                           double *, double *, int);
+
 // ------------------------------------------------------------ propagators
 
 // Fv[s+1] = F(U[s]) for s in [first, first+count).
@@ -304,6 +252,12 @@ static parareal_status coarse_apply_t(parareal_ctx *c, const double *Uin, int s,
 {
     T *cA = static_cast<T *>(c->cA), *cB = static_cast<T *>(c->cB), *cC = static_cast<T *>(c->cC),
       *cD = static_cast<T *>(c->cD);
+    if (c->cfg.coarse_kind != PARAREAL_COARSE_STENCIL) {
+        // shift + convolution net, on the fine grid or on the restricted grid
+        if (c->r == 1) return net_apply<double, double>(c, Uin, s, static_cast<double *>(out));
+        LK(launch_restrict<T>(Uin, c->n, c->r, cA, c->st));
+        return net_apply<T, T>(c, cA, s, static_cast<T *>(out));
+    }
     if (c->r > 1) {
         LK(launch_restrict<T>(Uin, c->n, c->r, cA, c->st));
         return rk4_batch<T>(c, c->nc, cA, static_cast<T *>(out), s, 1, c->Nc, c->cfg.dt_coarse,
@@ -360,27 +314,67 @@ static parareal_status coarse_chain(parareal_ctx *c, int first, int count, bool 
     return PARAREAL_OK;
 }
 
-static parareal_status read_norms(parareal_ctx *c, int from, int to)
+// Device work of one Parareal iteration (Algorithm 1 loop body for every
+// open slice), enqueued on c->st without any host synchronisation:
+// fine sweep of slices K..N-1, then the serial coarse sweep with the
+// correction and per-slice norms, then (with a reference) the defect norms
+// into slot N+1 of slice_norms.  K = c->k_total: U[0..K] are already exact.
+parareal_status iter_enqueue(parareal_ctx *c)
 {
-    CK(cudaMemcpyAsync(c->h_norms, c->slice_norms, sizeof(double) * 5 * (c->N + 1),
+    const int K = c->k_total;
+    parareal_status s = DISPATCH(c, fine_sweep_t, K, c->N - K);
+    if (s != PARAREAL_OK) return s;
+    // slice K+1: its input U[K] did not change, so G's difference is zero
+    s = DISPATCH(c, correct_t, K, c->gold[K + 1], c->gold[K + 1], true);
+    if (s != PARAREAL_OK) return s;
+    for (int n = K + 1; n < c->N; ++n) {
+        s = DISPATCH(c, coarse_apply_t, c->U + (long long)n * c->P, n, c->gspare);
+        if (s != PARAREAL_OK) return s;
+        s = DISPATCH(c, correct_t, n, c->gspare, c->gold[n + 1], true);
+        if (s != PARAREAL_OK) return s;
+        std::swap(c->gspare, c->gold[n + 1]);
+    }
+    if (c->has_ref) {
+        LK(launch_diff_norms<double>(c->U + (long long)c->N * c->P, c->ref, c->P, c->partials, c->nblk, c->st));
+        LK(launch_reduce_partials(c->partials, c->nblk, c->slice_norms + 5ll * (c->N + 1), c->st));
+    }
+    CK(cudaMemcpyAsync(c->h_norms, c->slice_norms, sizeof(double) * 5 * (c->N + 2),
                        cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
+    return PARAREAL_OK;
+}
+
+// Host side of one iteration, after c->st has been synchronised: per-slice
+// and maximal relative changes, the defect (or -1), NaN/Inf detection.
+parareal_status iter_finish(parareal_ctx *c, double *dmax, double *l2max, double *d)
+{
+    const int K = c->k_total;
+    *dmax = 0.0;
+    *l2max = 0.0;
     for (int s = 0; s <= c->N; ++s) {
-        if (s < from || s > to) { c->diff_inf[s] = 0.0; c->diff_l2[s] = 0.0; continue; }
+        if (s < K + 1) { c->diff_inf[s] = 0.0; c->diff_l2[s] = 0.0; continue; }
         const double *q = c->h_norms + 5 * s;
         if (q[4] != 0.0) return fail(c, PARAREAL_E_DIVERGED, "non-finite value in slice " + std::to_string(s));
         c->diff_inf[s] = q[1] > 0 ? q[0] / q[1] : q[0];
         c->diff_l2[s] = q[3] > 0 ? std::sqrt(q[2] / q[3]) : std::sqrt(q[2]);
+        *dmax = std::max(*dmax, c->diff_inf[s]);
+        *l2max = std::max(*l2max, c->diff_l2[s]);
     }
+    *d = -1.0;
+    if (c->has_ref) {
+        const double *q = c->h_norms + 5 * (c->N + 1);
+        if (q[4] != 0.0) return fail(c, PARAREAL_E_DIVERGED, "non-finite value in the last slice");
+        *d = q[1] > 0 ? q[0] / q[1] : q[0];
+    }
+    c->k_total++;
     return PARAREAL_OK;
 }
 
 static parareal_status defect(parareal_ctx *c, double *d)
 {
     LK(launch_diff_norms<double>(c->U + (long long)c->N * c->P, c->ref, c->P, c->partials, c->nblk, c->st));
-    LK(launch_reduce_partials(c->partials, c->nblk, c->slice_norms, c->st));
+    LK(launch_reduce_partials(c->partials, c->nblk, c->slice_norms + 5ll * (c->N + 1), c->st));
     double h[5];
-    CK(cudaMemcpyAsync(h, c->slice_norms, sizeof h, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(h, c->slice_norms + 5ll * (c->N + 1), sizeof h, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     if (h[4] != 0.0) return fail(c, PARAREAL_E_DIVERGED, "non-finite value in the last slice");
     *d = h[1] > 0 ? h[0] / h[1] : h[0];
@@ -450,16 +444,24 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
     ok = ok && alloc(&c->wS, P * e);
     c->nblk = correct_blocks(c->P);
     ok = ok && alloc((void **)&c->partials, 5 * sizeof(double) * (size_t)c->nblk);
-    ok = ok && alloc((void **)&c->slice_norms, 5 * sizeof(double) * (N + 1));
-    ok = ok && cudaMallocHost((void **)&c->h_norms, 5 * sizeof(double) * (N + 1)) == cudaSuccess;
+    ok = ok && alloc((void **)&c->slice_norms, 5 * sizeof(double) * (N + 2));
+    ok = ok && cudaMallocHost((void **)&c->h_norms, 5 * sizeof(double) * (N + 2)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         parareal_destroy(c);
         return fail(nullptr, PARAREAL_E_NOMEM, "device allocation failed");
     }
-    if (cudaMemsetAsync(c->slice_norms, 0, 5 * sizeof(double) * (N + 1), c->st) != cudaSuccess) {
+    if (cudaMemsetAsync(c->slice_norms, 0, 5 * sizeof(double) * (N + 2), c->st) != cudaSuccess) {
         parareal_destroy(c);
         return fail(nullptr, PARAREAL_E_CUDA, "memset failed");
+    }
+    if (cfg->coarse_kind != PARAREAL_COARSE_STENCIL) {
+        parareal_status ns = net_setup(c);
+        if (ns != PARAREAL_OK) {
+            const std::string msg = c->err;
+            parareal_destroy(c);
+            return fail(nullptr, ns, msg);
+        }
     }
     *out = c;
     return warn;
@@ -477,6 +479,7 @@ extern "C" void parareal_destroy(parareal_ctx *c)
         if (p) cudaFree(p);
     if (c->h_norms) cudaFreeHost(c->h_norms);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    net_free(c);
     delete c;
 }
 
@@ -627,32 +630,12 @@ extern "C" parareal_status parareal_iterate(parareal_ctx *c, int k_max, double t
     const auto t0 = std::chrono::steady_clock::now();
     int done = 0;
     for (; done < k_max && c->k_total < c->N; ++done) {
-        const int K = c->k_total;   // U[0..K] are exact
-        s = DISPATCH(c, fine_sweep_t, K, c->N - K);
+        s = iter_enqueue(c);
         if (s != PARAREAL_OK) return s;
-        // slice K+1: its input U[K] did not change, so G's difference is zero
-        s = DISPATCH(c, correct_t, K, c->gold[K + 1], c->gold[K + 1], true);
+        CK(cudaStreamSynchronize(c->st));
+        double dmax, l2max, d;
+        s = iter_finish(c, &dmax, &l2max, &d);
         if (s != PARAREAL_OK) return s;
-        for (int n = K + 1; n < c->N; ++n) {
-            s = DISPATCH(c, coarse_apply_t, c->U + (long long)n * c->P, n, c->gspare);
-            if (s != PARAREAL_OK) return s;
-            s = DISPATCH(c, correct_t, n, c->gspare, c->gold[n + 1], true);
-            if (s != PARAREAL_OK) return s;
-            std::swap(c->gspare, c->gold[n + 1]);
-        }
-        s = read_norms(c, K + 1, c->N);
-        if (s != PARAREAL_OK) return s;
-        c->k_total++;
-        double dmax = 0.0, l2max = 0.0;
-        for (int n = 0; n <= c->N; ++n) {
-            dmax = std::max(dmax, c->diff_inf[n]);
-            l2max = std::max(l2max, c->diff_l2[n]);
-        }
-        double d = -1.0;
-        if (c->has_ref) {
-            s = defect(c, &d);
-            if (s != PARAREAL_OK) return s;
-        }
         if (hist) {
             hist[4 * done + 0] = dmax;
             hist[4 * done + 1] = l2max;

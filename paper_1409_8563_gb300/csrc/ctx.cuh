@@ -1,0 +1,109 @@
+// ctx.cuh -- the context behind the opaque parareal_ctx handle, shared by
+// the host-side translation units (api.cu, learned.cu).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+
+enum { PATH_FUSED = 0, PATH_STAGED = 1 };
+
+// Device state of the learned coarse propagator (allocated on demand).
+struct NetState {
+    int m = 0;                 // grid edge the net runs on (n / coarse_factor)
+    long long Pm = 0;
+    int shift[3] = {0, 0, 0};  // periodic shift S, in cells, normalised to [0, m)
+    int bmax = 0;              // batch capacity of the training buffers
+    float *master = nullptr, *grad = nullptr, *mom1 = nullptr, *mom2 = nullptr;
+    float *W1q = nullptr, *W4q = nullptr;
+    __nv_bfloat16 *B2f = nullptr, *B3f = nullptr, *B2b = nullptr, *B3b = nullptr;
+    float *nu_slices = nullptr;               // nu(t_n)/nu0 per slice
+    __nv_bfloat16 *ia = nullptr, *ib = nullptr;   // inference activations, 1 field each
+    // training buffers (bmax fields each)
+    float *z1 = nullptr, *z2 = nullptr, *z3 = nullptr;
+    __nv_bfloat16 *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *dzA = nullptr, *dzB = nullptr,
+                  *dz4 = nullptr;
+    float *ub = nullptr, *fb = nullptr, *nub = nullptr;
+    float *partials = nullptr;
+    double *loss_parts = nullptr, *loss_sum = nullptr;
+    float *h_nub = nullptr;                   // pinned staging for nu of a batch
+    double *h_loss = nullptr;
+    int adam_t = 0;
+    bool has_model = false;
+};
+
+struct parareal_ctx {
+    parareal_config cfg{};
+    cudaStream_t st = nullptr;
+    int dev = 0;
+    int n = 0, N = 0, r = 1, nc = 0;
+    long long P = 0, Pc = 0, Nf = 0, Nc = 0;
+    bool f64 = false;
+    size_t esz = 4;
+
+    double *U = nullptr;
+    void *Fv = nullptr;
+    std::vector<void *> gold;     // gold[s] = G(U^k[s-1]) for s = 1..N (index 0 unused)
+    void *gspare = nullptr;
+    void *wA = nullptr, *wB = nullptr, *wC = nullptr;
+    void *cA = nullptr, *cB = nullptr, *cC = nullptr, *cD = nullptr;
+    double *tmpd = nullptr;       // 2P doubles: conversions and propagate() scratch
+    void *wS = nullptr;           // P of T: state of the serial fine run
+    double *ref = nullptr;
+    double *partials = nullptr;
+    int nblk = 0;
+    double *slice_norms = nullptr;  // (N+1) x 5 on device
+    double *h_norms = nullptr;      // pinned copy
+
+    bool has_problem = false, started = false, has_ref = false;
+    int k_total = 0;
+    std::vector<double> diff_inf, diff_l2;   // last iteration, per slice
+
+    int fine_path = PATH_FUSED, fine_tx = 64, fine_ty = 16, fine_zc = 0;
+    int coarse_path = PATH_FUSED, coarse_tx = 32, coarse_ty = 8, coarse_zc = 0;
+
+    NetState net;
+
+    std::string err;
+    long long launches = 0;
+
+    // kernel timing (parareal_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;   // pairs: start, stop
+    size_t ev_used = 0;
+    double prof_bytes = 0.0;
+    long long prof_launches = 0;
+};
+
+parareal_status fail(parareal_ctx *c, parareal_status s, const std::string &msg);
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(c, PARAREAL_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define LK(call)                                                                              \
+    do {                                                                                      \
+        ++c->launches;                                                                        \
+        CK(call);                                                                             \
+    } while (0)
+
+template <typename T>
+parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, int first_slice, int count,
+                          long long nsteps, double dt, int path, int tx, int ty, int zc, T *ws1,
+                          T *ws2, T *ws3, int slice_stride = 1);
+
+// api.cu: one Parareal iteration split into device work and host bookkeeping
+parareal_status iter_enqueue(parareal_ctx *c);
+parareal_status iter_finish(parareal_ctx *c, double *dmax, double *l2max, double *d);
+
+// learned.cu
+parareal_status net_setup(parareal_ctx *c);
+void net_free(parareal_ctx *c);
+template <typename TU, typename TG>
+parareal_status net_apply(parareal_ctx *c, const TU *u, int slice, TG *out);

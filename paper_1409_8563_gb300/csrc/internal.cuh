@@ -20,6 +20,7 @@ struct StepArgs {
     long long P;              // n^3
     int count;                // number of fields (time slices) in the batch
     int first_slice;          // slice index of field 0 (for the time of each step)
+    int slice_stride;         // field f runs on slice first_slice + f * slice_stride
     long long steps_per_slice;// N_f or N_c: step index of slice s, step j = s*steps_per_slice + j
     long long j;              // step number within the slice
     double dt;

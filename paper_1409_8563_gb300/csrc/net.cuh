@@ -1,0 +1,51 @@
+// net.cuh -- layout constants and launchers of the learned coarse propagator.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace pr {
+
+// FP32 master parameters, in this order (tap = (dz+1)*9 + (dy+1)*3 + (dx+1)):
+//   W1[16][2][27] b1[16] W2[16][16][27] b2[16] W3[16][16][27] b3[16] W4[1][16][27] b4[1]
+constexpr int NET_W1 = 0, NET_B1 = 864, NET_W2 = 880, NET_B2 = 7792, NET_W3 = 7808,
+              NET_B3 = 14720, NET_W4 = 14736, NET_B4 = 15168, NET_PARAMS = 15169;
+constexpr int NET_MID_PARTIAL = 27 * 256 + 16;   // dW[27][16][16] + db[16]
+constexpr int NET_OUT_PARTIAL = 433;             // dW4[16][27] + db4
+constexpr int NET_IN_PARTIAL = 880;              // dW1[16][2][27] + db1[16]
+
+cudaError_t configure_net_kernels();
+template <typename TU>
+cudaError_t launch_net_in_fwd(const TU *u, int m, const int s[3], const float *nu_hat, int batch,
+                              const float *W1q, const float *b1, float *z1, __nv_bfloat16 *a1,
+                              cudaStream_t st);
+cudaError_t launch_net_mid(int mode, const __nv_bfloat16 *in, int m, int batch,
+                           const __nv_bfloat16 *Bt, const float *bias, const float *zaux, float *zout,
+                           __nv_bfloat16 *out, cudaStream_t st);
+int net_partial_blocks(int m, int batch);
+cudaError_t launch_net_mid_wgrad(const __nv_bfloat16 *x, const __nv_bfloat16 *dz, int m, int batch,
+                                 float *partials, int nblocks, cudaStream_t st);
+template <typename TU, typename TG>
+cudaError_t launch_net_out_fwd(const __nv_bfloat16 *a3, int m, int batch, const float *W4q,
+                               const float *b4, const TU *u, const int s[3], TG *g_out,
+                               const float *tgt, float grad_scale, __nv_bfloat16 *dz4,
+                               double *loss_partials, cudaStream_t st);
+cudaError_t launch_net_out_dgrad(const __nv_bfloat16 *dz4, int m, int batch, const float *W4q,
+                                 const float *z3, __nv_bfloat16 *dz3, cudaStream_t st);
+cudaError_t launch_net_out_wgrad(const __nv_bfloat16 *a3, const __nv_bfloat16 *dz4, int m, int batch,
+                                 float *partials, int nblocks, cudaStream_t st);
+template <typename TU>
+cudaError_t launch_net_in_wgrad(const TU *u, int m, int batch, const int s[3], const float *nu_hat,
+                                const __nv_bfloat16 *dz1, float *partials, int nblocks,
+                                cudaStream_t st);
+cudaError_t launch_reduce_cols(const float *partials, int nb, int stride, int L, float *out,
+                               cudaStream_t st);
+cudaError_t launch_reduce_mid(const float *partials, int nb, float *W, float *b, cudaStream_t st);
+cudaError_t launch_reduce_loss(const double *parts, int nb, double *out, cudaStream_t st);
+cudaError_t launch_adam(float *p, const float *g, float *mo, float *vo, int L, float lr, float b1,
+                        float b2, float eps, float c1, float c2, cudaStream_t st);
+cudaError_t launch_prepare_operands(const float *master, float *W1q, __nv_bfloat16 *B2f,
+                                    __nv_bfloat16 *B3f, __nv_bfloat16 *B2b, __nv_bfloat16 *B3b,
+                                    float *W4q, cudaStream_t st);
+
+}  // namespace pr

@@ -125,8 +125,21 @@ struct FusedShape {
     static constexpr int RY = TY + 8;
     static constexpr int QX = RX / V;          // vectors per region row
     static constexpr int NT = QX * RY;         // threads per CTA
-    static constexpr size_t SMEM = 2ull * 4 * RX * RY * sizeof(T);  // double-buffered stage planes
+    static constexpr int D = 4;                // planes of u in flight ahead of use
+    static constexpr int RING = D + 2;         // u planes resident: in flight + current + previous
+    static constexpr size_t SMEM = (size_t)(RING + 2 * 3) * RX * RY * sizeof(T);
 };
+
+// 16-byte asynchronous global->shared copy (L2 only, bypassing L1) and its
+// group bookkeeping.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(FusedShape<T, TX, TY>::NT, 1)
@@ -136,8 +149,10 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
     using S = FusedShape<T, TX, TY>;
     constexpr int V = S::V, RX = S::RX, RY = S::RY, QX = S::QX;
     constexpr int PL = RX * RY;
+    constexpr int D = S::D, RING = S::RING;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *planes = reinterpret_cast<T *>(smem_raw);   // [2][4][RY][RX]
+    T *ring = reinterpret_cast<T *>(smem_raw);     // [RING][RY][RX]   u planes
+    T *planes = ring + RING * PL;                  // [2][3][RY][RX]   y2, y3, y4 planes
     __shared__ T s_w[3][7];                        // stage 1, stages 2-3, stage 4
 
     const int tid = threadIdx.x;
@@ -151,7 +166,7 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
     const int n = a.n;
 
     if (tid < 3) {
-        const long long s = (long long)(a.first_slice + f) * a.steps_per_slice + a.j;
+        const long long s = (long long)(a.first_slice + f * a.slice_stride) * a.steps_per_slice + a.j;
         const double t = (double)s * a.dt;
         const double ts = a.frozen ? t : (tid == 0 ? t : (tid == 1 ? t + 0.5 * a.dt : t + a.dt));
         double w[7];
@@ -188,18 +203,37 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
     T U[4][V] = {}, Y2[2][V] = {}, Y3[2][V] = {}, Y4[2][V] = {}, A[3][V] = {};
     constexpr T c6 = (T)(1.0 / 6.0), c3 = (T)(1.0 / 3.0), hf = (T)0.5;
 
+    // u plane z lives in ring slot (z - z_lo + 4) mod RING; plane zi + D is
+    // requested while plane zi is consumed, so DRAM latency overlaps D
+    // iterations of compute.
+    const int z_end = z_hi + 4;
+    const int my = ry * RX + qx * V;
+    // z >= z_lo - 5 everywhere below, so the offset keeps the index non-negative
+    auto slot = [&](int z) { return ring + ((z - z_lo + 4 + RING) % RING) * PL; };
+    auto request = [&](int z) {
+        if (z < z_end) {
+            const int zw = ((z % n) + n) % n;
+            cp_async16(slot(z) + my, src + (long long)zw * plane);
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int q = 0; q < D; ++q) request(z_lo - 4 + q);
+
     int cur = 0;
-    for (int zi = z_lo - 4; zi < z_hi + 4; ++zi) {
-        const int zw = ((zi % n) + n) % n;
+    for (int zi = z_lo - 4; zi < z_end; ++zi) {
+        request(zi + D);
+        cp_async_wait<D>();
         T un[V];
-        ldg_v<T>(src + (long long)zw * plane, un);
-        const T *Sc = planes + cur * 4 * PL;
-        T *Sn = planes + (cur ^ 1) * 4 * PL;
+        ldv<T>(slot(zi) + my, un);
+        const T *Su = slot(zi - 1);                   // u at plane zi-1 (complete since last barrier)
+        const T *Sc = planes + cur * 3 * PL;          // y2(zi-2), y3(zi-3), y4(zi-4)
+        T *Sn = planes + (cur ^ 1) * 3 * PL;
         T d[V];
         T y2n[V] = {}, y3n[V] = {}, y4n[V] = {}, accn[V] = {};
         // stage 1 at plane zi-1
         if (act1) {
-            stage_delta<T, RX, RY>(d, Sc, qx, ry, U[0], U[1], un, w1);
+            stage_delta<T, RX, RY>(d, Su, qx, ry, U[0], U[1], un, w1);
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 y2n[i] = fma(hf, d[i], U[0][i]);
@@ -208,7 +242,7 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
         }
         // stage 2 at plane zi-2
         if (act2) {
-            stage_delta<T, RX, RY>(d, Sc + PL, qx, ry, Y2[0], Y2[1], y2n, w2);
+            stage_delta<T, RX, RY>(d, Sc, qx, ry, Y2[0], Y2[1], y2n, w2);
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 y3n[i] = fma(hf, d[i], U[1][i]);
@@ -217,7 +251,7 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
         }
         // stage 3 at plane zi-3
         if (act3) {
-            stage_delta<T, RX, RY>(d, Sc + 2 * PL, qx, ry, Y3[0], Y3[1], y3n, w2);
+            stage_delta<T, RX, RY>(d, Sc + PL, qx, ry, Y3[0], Y3[1], y3n, w2);
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 y4n[i] = U[2][i] + d[i];
@@ -226,7 +260,7 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
         }
         // stage 4 at plane zi-4: the finished step
         if (act4) {
-            stage_delta<T, RX, RY>(d, Sc + 3 * PL, qx, ry, Y4[0], Y4[1], y4n, w4);
+            stage_delta<T, RX, RY>(d, Sc + 2 * PL, qx, ry, Y4[0], Y4[1], y4n, w4);
             const int zo = zi - 4;
             if (owner && zo >= z_lo) {
                 T o[V];
@@ -235,10 +269,9 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
                 stv<T>(dst + (long long)zo * plane, o);
             }
         }
-        stv<T>(Sn + ry * RX + qx * V, un);
-        stv<T>(Sn + PL + ry * RX + qx * V, y2n);
-        stv<T>(Sn + 2 * PL + ry * RX + qx * V, y3n);
-        stv<T>(Sn + 3 * PL + ry * RX + qx * V, y4n);
+        stv<T>(Sn + my, y2n);
+        stv<T>(Sn + PL + my, y3n);
+        stv<T>(Sn + 2 * PL + my, y4n);
         __syncthreads();
         cur ^= 1;
 #pragma unroll
@@ -250,6 +283,7 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
             A[2][i] = A[1][i]; A[1][i] = A[0][i]; A[0][i] = accn[i];
         }
     }
+    cp_async_wait<0>();
 }
 
 template <typename T, int TX, int TY>
@@ -321,7 +355,7 @@ rk4_stage_kernel(StepArgs a, int stage, const T *__restrict__ ysrc, T *__restric
     __shared__ T s_w[7];
     const int f = blockIdx.y;
     if (threadIdx.x == 0) {
-        const long long s = (long long)(a.first_slice + f) * a.steps_per_slice + a.j;
+        const long long s = (long long)(a.first_slice + f * a.slice_stride) * a.steps_per_slice + a.j;
         const double t = (double)s * a.dt;
         const double c = (stage == 1 || a.frozen) ? 0.0 : (stage == 4 ? 1.0 : 0.5);
         double w[7];

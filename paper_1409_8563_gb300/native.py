@@ -52,6 +52,16 @@ class Config(ctypes.Structure):
                    int(allow_unstable))
 
 
+MODEL_PARAMS = 15169
+
+
+class TrainConfig(ctypes.Structure):
+    """Mirror of parareal_train_config."""
+    _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
+                ("seed", ctypes.c_ulonglong)]
+
+
 _lib = None
 
 # name -> (restype, argtypes)
@@ -70,6 +80,11 @@ SIGNATURES = {
     "parareal_get_slice": (_i, [_vp, _i, _vp, _i, _i]),
     "parareal_set_slice": (_i, [_vp, _i, _vp, _i, _i]),
     "parareal_propagate": (_i, [_vp, _i, _vp, _vp, _i, _i, _i]),
+    "parareal_set_coarse_model": (_i, [_vp, _vp, _i]),
+    "parareal_get_coarse_model": (_i, [_vp, _vp, _i]),
+    "parareal_make_pairs": (_i, [_vp, _vp, _i, _vp, _vp, _ip]),
+    "parareal_train_coarse": (_i, [_vp, _vp, _vp, _ip, _i, _vp, _dp]),
+    "parareal_coarse_model_grad": (_i, [_vp, _vp, _vp, _ip, _i, _vp, _dp]),
     "parareal_profile": (_i, [_vp, _i]),
     "parareal_profile_read": (_i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]),
     "parareal_launch_count": (ctypes.c_longlong, [_vp]),
@@ -188,6 +203,52 @@ class Parareal:
         if code != code2 or mem != MEM_DEVICE or mem2 != MEM_DEVICE:
             raise ValueError("propagate needs device tensors of one dtype")
         return self._check(lib().parareal_propagate(self._h, which, ps, pd, code, first, count))
+
+    # ------------------------------------------------ learned coarse propagator
+
+    def set_coarse_model(self, w):
+        """w: MODEL_PARAMS float32 values (numpy host array or CUDA tensor)."""
+        p, code, mem, _k = _field(w)
+        if code != F32:
+            raise ValueError("model weights are float32")
+        return self._check(lib().parareal_set_coarse_model(self._h, p, mem))
+
+    def get_coarse_model(self):
+        out = np.empty(MODEL_PARAMS, dtype=np.float32)
+        self._check(lib().parareal_get_coarse_model(self._h, ctypes.c_void_p(out.ctypes.data), MEM_HOST))
+        return out
+
+    def make_pairs(self, ics, pairs_u, pairs_f):
+        """ics: [n_ics, n, n, n] float32 CUDA tensor; pairs_*: [n_ics*N, m, m, m]
+        float32 CUDA tensors.  Returns the slice index of every pair."""
+        n_ics = ics.shape[0]
+        sl = (ctypes.c_int * (n_ics * self.cfg.n_slices))()
+        self._check(lib().parareal_make_pairs(self._h, ctypes.c_void_p(ics.data_ptr()), n_ics,
+                                              ctypes.c_void_p(pairs_u.data_ptr()),
+                                              ctypes.c_void_p(pairs_f.data_ptr()), sl))
+        return np.array(sl[:], dtype=np.int32)
+
+    def train_coarse(self, pairs_u, pairs_f, pair_slice, epochs, batch, lr=1e-3, beta1=0.9,
+                     beta2=0.999, eps=1e-8, seed=0):
+        tc = TrainConfig(int(epochs), int(batch), float(lr), float(beta1), float(beta2), float(eps),
+                         int(seed))
+        n = len(pair_slice)
+        sl = (ctypes.c_int * n)(*[int(v) for v in pair_slice])
+        hist = (ctypes.c_double * max(1, epochs))()
+        self._check(lib().parareal_train_coarse(self._h, ctypes.c_void_p(pairs_u.data_ptr()),
+                                                ctypes.c_void_p(pairs_f.data_ptr()), sl, n,
+                                                ctypes.byref(tc), hist))
+        return np.array(hist[:epochs])
+
+    def coarse_model_grad(self, u, target, slices, grad_out):
+        n = len(slices)
+        sl = (ctypes.c_int * n)(*[int(v) for v in slices])
+        loss = ctypes.c_double()
+        self._check(lib().parareal_coarse_model_grad(self._h, ctypes.c_void_p(u.data_ptr()),
+                                                     ctypes.c_void_p(target.data_ptr()), sl, n,
+                                                     ctypes.c_void_p(grad_out.data_ptr()),
+                                                     ctypes.byref(loss)))
+        return loss.value
 
     def profile(self, enable=True):
         return self._check(lib().parareal_profile(self._h, int(enable)))

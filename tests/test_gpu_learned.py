@@ -1,0 +1,203 @@
+"""GPU parity of the learned coarse propagator (forward, gradients, Adam,
+pair generation) against the FP64 oracle, and what training buys Parareal.
+
+Tolerances: the oracle rounds to bfloat16 at the same points as the GPU
+(weights, network input, activations, pre-activation gradients), so the two
+differ only where FP32 and FP64 accumulation put a value on different sides
+of a bfloat16 rounding boundary (one bf16 ulp = 2^-8 relative on those
+elements).  Relative L2 of the network output and of each layer's gradient is
+therefore held to 1e-2; FP32-only arithmetic (Adam, pairs) to 1e-5 / 1e-6.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import core, net
+from oracle import parareal as opr
+from paper_1409_8563_gb300 import configs, inputs, native
+from tests.helpers import oracle_F, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NET_TOL = 1e-2
+
+
+def learned_cfg(n=16, N=4, kind=native.COARSE_LEARNED, r=1):
+    base, _ = configs.small(n=n, n_slices=N, dtype=native.F32, nf=8, nc=2)
+    base.coarse_kind = kind
+    base.coarse_factor = r
+    return base
+
+
+def to_master(params):
+    flat = []
+    for W, b in params:
+        flat.append(W.ravel())
+        flat.append(b.ravel())
+    out = np.concatenate(flat).astype(np.float32)
+    assert out.size == native.MODEL_PARAMS
+    return out
+
+
+def from_master(v):
+    params, off = [], 0
+    for ci, co in net.LAYERS:
+        W = v[off:off + co * ci * 27].reshape(co, ci, 3, 3, 3).astype(np.float64)
+        off += co * ci * 27
+        b = v[off:off + co].astype(np.float64)
+        off += co
+        params.append([W, b])
+    return params
+
+
+def shift_of(cfg):
+    m = cfg.n // cfg.coarse_factor
+    return tuple(int(round(a * cfg.T / cfg.n_slices * m)) % m for a in cfg.a)
+
+
+def nu_hat(cfg, s):
+    t = s * cfg.T / cfg.n_slices
+    return float(np.float32((1 + cfg.nu_amp * math.sin(cfg.nu_omega * t))))
+
+
+def test_forward_matches_oracle():
+    cfg = learned_cfg()
+    ctx = native.Parareal(cfg)
+    params = net.init_params(seed=3, scale=0.15)
+    w = to_master(params)
+    ctx.set_coarse_model(w)
+    params = from_master(w)           # the FP32 values the GPU holds
+    u = inputs.spectral_ic(16, seed=5, kmax=4)
+    src = torch.from_numpy(u).float().cuda().contiguous()
+    dst = torch.empty_like(src)
+    s = 2
+    ctx.propagate(1, src, dst, s, 1)
+    got = dst.double().cpu().numpy()
+    u32 = u.astype(np.float32).astype(np.float64)
+    ref, _ = net.forward(u32, nu_hat(cfg, s), params, shift_of(cfg), bf16_emul=True)
+    su = core.shift(u32, shift_of(cfg))
+    assert np.max(np.abs(ref - su)) > 1e-2          # the net contributes
+    err = rel_l2(got - su, ref - su)
+    assert err < NET_TOL, err
+    ctx.close()
+
+
+def test_shift_only_propagator_is_the_exact_shift():
+    cfg = learned_cfg(kind=native.COARSE_SHIFT)
+    ctx = native.Parareal(cfg)
+    u = inputs.spectral_ic(16, seed=6, kmax=4)
+    src = torch.from_numpy(u).cuda().contiguous()
+    dst = torch.empty_like(src)
+    ctx.propagate(1, src, dst, 1, 1)
+    assert np.array_equal(dst.cpu().numpy(), core.shift(u, shift_of(cfg)))
+    ctx.close()
+
+
+def test_gradients_match_oracle():
+    cfg = learned_cfg()
+    ctx = native.Parareal(cfg)
+    params = net.init_params(seed=4, scale=0.15)
+    w = to_master(params)
+    ctx.set_coarse_model(w)
+    params = from_master(w)
+    us = [inputs.spectral_ic(16, seed=10 + i, kmax=4) for i in range(2)]
+    tg = [core.shift(x, shift_of(cfg)) * 0.9 + 0.05 * inputs.spectral_ic(16, seed=20 + i, kmax=6)
+          for i, x in enumerate(us)]
+    us32 = [x.astype(np.float32) for x in us]
+    tg32 = [x.astype(np.float32) for x in tg]
+    slices = [1, 3]
+    U = torch.from_numpy(np.stack(us32)).cuda()
+    Tg = torch.from_numpy(np.stack(tg32)).cuda()
+    g = torch.empty(native.MODEL_PARAMS, dtype=torch.float32, device="cuda")
+    loss = ctx.coarse_model_grad(U, Tg, slices, g)
+    ref_loss, ref_g = net.loss_and_grads([x.astype(np.float64) for x in us32],
+                                         [nu_hat(cfg, s) for s in slices],
+                                         [x.astype(np.float64) for x in tg32], params,
+                                         shift_of(cfg), bf16_emul=True)
+    assert abs(loss - ref_loss) <= 1e-3 * ref_loss, (loss, ref_loss)
+    got = from_master(g.cpu().numpy())
+    for li in range(4):
+        for k in range(2):
+            e = rel_l2(got[li][k], ref_g[li][k])
+            assert e < 2 * NET_TOL, (li, k, e)
+    ctx.close()
+
+
+def test_adam_step_is_the_textbook_update_of_the_gpu_gradient():
+    cfg = learned_cfg()
+    ctx = native.Parareal(cfg)
+    w0 = to_master(net.init_params(seed=7, scale=0.1))
+    ctx.set_coarse_model(w0)
+    u = np.stack([inputs.spectral_ic(16, seed=30, kmax=4)]).astype(np.float32)
+    f = np.stack([inputs.spectral_ic(16, seed=31, kmax=4)]).astype(np.float32)
+    U, Fd = torch.from_numpy(u).cuda(), torch.from_numpy(f).cuda()
+    g = torch.empty(native.MODEL_PARAMS, dtype=torch.float32, device="cuda")
+    ctx.coarse_model_grad(U, Fd, [2], g)
+    grad = g.cpu().numpy().astype(np.float64)
+    ctx.train_coarse(U, Fd, [2], epochs=1, batch=1, lr=1e-3, eps=1e-8)
+    w1 = ctx.get_coarse_model().astype(np.float64)
+    p = [[w0.astype(np.float64).copy(), np.zeros(1)]]
+    m = net.zeros_like_params(p)
+    v = net.zeros_like_params(p)
+    net.adam_step(p, [[grad, np.zeros(1)]], m, v, 1, lr=1e-3, eps=1e-8)
+    assert np.max(np.abs(w1 - p[0][0])) <= 1e-6 * max(1.0, np.max(np.abs(w0)))
+    ctx.close()
+
+
+def test_pairs_follow_the_fine_trajectories():
+    cfg = learned_cfg(n=16, N=3)
+    ctx = native.Parareal(cfg)
+    ics = np.stack([inputs.spectral_ic(16, seed=40 + i, kmax=4) for i in range(2)]).astype(np.float32)
+    pu = torch.empty((6, 16, 16, 16), dtype=torch.float32, device="cuda")
+    pf = torch.empty_like(pu)
+    sl = ctx.make_pairs(torch.from_numpy(ics).cuda(), pu, pf)
+    assert list(sl) == [0, 1, 2, 0, 1, 2]
+    F = oracle_F(cfg)
+    for i in range(2):
+        x = ics[i].astype(np.float64)
+        for n in range(3):
+            assert rel_l2(pu[i * 3 + n].double().cpu().numpy(), x) < 1e-5
+            x = F(x, n)
+            assert rel_l2(pf[i * 3 + n].double().cpu().numpy(), x) < 1e-5
+    ctx.close()
+
+
+def test_training_reduces_parareal_iterations():
+    """The trained net beats the untrained one (G = S) as Parareal's coarse
+    propagator: fewer iterations to the same defect."""
+    n, N = 32, 8
+    nu_max = 0.015
+    m = max(6, math.ceil(math.log2(12.0 * nu_max * n * n / 1.5)))
+    dt = 2.0 ** -m
+    T = 1.0
+    nf = round(T / N / dt)
+    def make(kind):
+        c = native.Config.make(n, N, T, dt, T / N, 1, fine_dtype=native.F32, coarse_kind=kind,
+                               nu0=0.01, nu_amp=0.5, nu_omega=2 * math.pi)
+        return c
+    ctx = native.Parareal(make(native.COARSE_LEARNED))
+    ics = np.stack([inputs.spectral_ic(n, seed=100 + i, kmax=6) for i in range(16)]).astype(np.float32)
+    pu = torch.empty((16 * N, n, n, n), dtype=torch.float32, device="cuda")
+    pf = torch.empty_like(pu)
+    sl = ctx.make_pairs(torch.from_numpy(ics).cuda(), pu, pf)
+    ctx.set_coarse_model(to_master(net.init_params(seed=0)))
+    hist = ctx.train_coarse(pu, pf, sl, epochs=40, batch=8, lr=2e-3, seed=1)
+    assert hist[-1] < 0.5 * hist[0], hist
+    u0 = torch.from_numpy(inputs.spectral_ic(n, seed=7, kmax=6)).cuda()
+
+    def iterations(c):
+        c.set_problem(u0)
+        c.serial_fine(None, as_reference=True)
+        k, h = c.iterate(N, 1e-6, native.STOP_DEFECT)
+        return k, h[:, 2]
+
+    k_learned, d_learned = iterations(ctx)
+    shift_ctx = native.Parareal(make(native.COARSE_SHIFT))
+    k_shift, d_shift = iterations(shift_ctx)
+    assert d_learned[-1] <= 1e-6 and d_shift[-1] <= 1e-6
+    assert k_learned < k_shift, (k_learned, k_shift, d_learned, d_shift)
+    assert d_learned[0] < d_shift[0]
+    ctx.close()
+    shift_ctx.close()
