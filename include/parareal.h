@@ -218,6 +218,42 @@ parareal_status parareal_coarse_model_grad(parareal_ctx *ctx, const float *u, co
                                            const int *slices, int count, float *grad_out,
                                            double *loss);
 
+/* Autotuner: times every compiled launch shape of the fine step kernel (tile
+ * in x and y, z-march chunk, or the per-stage path) on this context's batch
+ * of slices, and of the coarse step kernel on the coarse grid, keeps the
+ * fastest, and appends it to `cache_path` (JSON lines keyed by grid edge,
+ * dtype, batch size and SM count; NULL = no cache).  A cached key is reused
+ * without timing.  Uses the iterate as scratch: call before
+ * parareal_set_problem.  ms2 (may be NULL): best fine / coarse ms per step
+ * (-1 when taken from the cache). */
+parareal_status parareal_autotune(parareal_ctx *ctx, const char *cache_path, double *ms2);
+
+/* The launch shapes in use: {path (0 fused, 1 per-stage), tile_x, tile_y, z chunk}. */
+parareal_status parareal_get_launch_shape(const parareal_ctx *ctx, int *fine4, int *coarse4);
+
+/* Batches of independent problems of uneven sizes.  Each instance is a
+ * context of its own (its own config, workspace and stream); one round of
+ * the batch (the coarse start-up, or one iteration of every instance not yet
+ * stopped) is one CUDA graph whose parallel branches are the instances.
+ * There is no counterpart in the paper, which runs one problem. */
+typedef struct parareal_batch parareal_batch;
+parareal_status parareal_batch_create(const parareal_config *cfgs, int count, void *cuda_stream,
+                                      parareal_batch **out);
+parareal_status parareal_batch_set_problem(parareal_batch *b, int i, const void *u0, int dtype, int mem);
+/* Serial fine run of every instance (concurrently); as_reference as in parareal_serial_fine. */
+parareal_status parareal_batch_serial_fine(parareal_batch *b, int as_reference);
+/* Up to k_max rounds; every instance stops on its own rule.  k_done and defect
+ * (host, count entries each, may be NULL): iterations run and last d^k (-1 without reference). */
+parareal_status parareal_batch_iterate(parareal_batch *b, int k_max, double tol, int stop_rule,
+                                       int *k_done, double *defect);
+/* Autotune once per distinct (n, n/coarse_factor, dtype, N_p); call before set_problem. */
+parareal_status parareal_batch_autotune(parareal_batch *b, const char *cache_path);
+/* The context of instance i (owned by the batch; use it for get_slice etc.). */
+parareal_ctx *parareal_batch_context(parareal_batch *b, int i);
+long long parareal_batch_graph_launches(const parareal_batch *b);
+const char *parareal_batch_last_error(const parareal_batch *b);
+void parareal_batch_destroy(parareal_batch *b);
+
 /* Kernel timing.  While enabled, the context records a pair of CUDA events
  * (on its stream) around every launch of the fine propagator's step kernel
  * and accumulates them; parareal_profile_read synchronises the stream and

@@ -26,7 +26,7 @@ import math
 import numpy as np
 
 from . import inputs
-from .native import (COARSE_STENCIL, F32, F64, NU_FROZEN, NU_STAGE, Config)
+from .native import (COARSE_STENCIL, F32, F64, NU_FROZEN, NU_STAGE, Config, stability)
 
 NU_BASE = dict(nu0=0.01, nu_amp=0.5, nu_omega=2 * math.pi)
 
@@ -86,10 +86,15 @@ def small(n=32, n_slices=4, dtype=F64, r=1, nf=32, nc=4, seed=0, ic="spectral"):
     nco = n // r
     need = math.ceil(12.0 * nu_max * nco * nco * slice_len / 1.5 - 1e-9)
     nc = min(max(nc, need, 1), nf)
-    while nf % nc:          # ends at nc = nf at the latest
+    while True:
+        while nf % nc:      # ends at nc = nf at the latest
+            nc += 1
+        cfg = Config.make(n, n_slices, n_slices * slice_len, dt_f, slice_len / nc, r,
+                          fine_dtype=dtype, **NU_BASE)
+        # advection can destabilise a step that diffusion alone allows
+        if nc >= nf or stability(cfg)[0] == 0:
+            break
         nc += 1
-    cfg = Config.make(n, n_slices, n_slices * slice_len, dt_f, slice_len / nc, r,
-                      fine_dtype=dtype, **NU_BASE)
     if ic == "spectral":
         u0 = inputs.spectral_ic(n, seed=seed, kmax=max(2, n // 8))
     else:

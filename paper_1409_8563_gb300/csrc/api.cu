@@ -14,6 +14,7 @@
 //   tmpd   2P         FP64   host/device conversions, propagate() scratch
 //   ref    P          FP64   u_fine(T) for the defect d^k (optional)
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -397,6 +398,16 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
     if (parareal_stability(cfg, growth) == PARAREAL_E_UNSTABLE) {
         if (!cfg->allow_unstable) return PARAREAL_E_UNSTABLE;
         warn = PARAREAL_W_MARGINAL;
+    }
+    {
+        // shared-memory opt-ins, once per device and process
+        static std::vector<int> configured;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, PARAREAL_E_CUDA, "no CUDA device");
+        if (std::find(configured.begin(), configured.end(), dev) == configured.end()) {
+            if (configure_rk4_kernels() != cudaSuccess) return fail(nullptr, PARAREAL_E_CUDA, "kernel configuration failed");
+            configured.push_back(dev);
+        }
     }
     parareal_ctx *c = new parareal_ctx();
     c->cfg = *cfg;
@@ -815,4 +826,161 @@ extern "C" parareal_status parareal_propagate(parareal_ctx *c, int which, const 
     if (dtype != PARAREAL_F32 && dtype != PARAREAL_F64) return fail(c, PARAREAL_E_INVALID, "dtype");
     if (first < 0 || count < 0 || first + count > c->N) return fail(c, PARAREAL_E_INVALID, "slice range");
     return DISPATCH(c, propagate_t, which, src, dst, dtype, first, count);
+}
+
+// ----------------------------------------------------------------- autotune
+
+// Time `reps` RK4 steps of `count` fields on an m^3 grid with one launch
+// shape; returns ms per step (min over 3 trials).
+template <typename T>
+static parareal_status time_shape(parareal_ctx *c, int m, int count, int path, int tx, int ty, int zc,
+                                  double dt, double *ms)
+{
+    T *in = static_cast<T *>(c->wC), *out = static_cast<T *>(c->Fv) + c->P;
+    T *w1 = static_cast<T *>(c->wA), *w2 = static_cast<T *>(c->wB);
+    T *w3 = reinterpret_cast<T *>(c->U);   // scratch: autotune overwrites the iterate
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int reps = 4;
+    double best = 1e30;
+    parareal_status s = PARAREAL_OK;
+    for (int trial = 0; trial < 3 && s == PARAREAL_OK; ++trial) {
+        CK(cudaEventRecord(e0, c->st));
+        s = rk4_batch<T>(c, m, in, out, 0, count, reps, dt, path, tx, ty, zc, w1, w2, w3);
+        CK(cudaEventRecord(e1, c->st));
+        CK(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, e0, e1));
+        if (trial > 0) best = std::min(best, (double)t / reps);   // trial 0 warms up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = best;
+    return s;
+}
+
+// Candidates: every compiled fused shape that divides m, whole-column and
+// chunked z marches, and the per-stage path.
+static void candidates(int dtype, int m, std::vector<std::array<int, 4>> *out)
+{
+    const int shapes[][2] = {{64, 16}, {64, 8}, {32, 16}, {32, 8}, {16, 16}, {16, 8}};
+    for (auto &sh : shapes) {
+        if (!rk4_fused_supported(dtype, m, sh[0], sh[1])) continue;
+        for (int zc = m; zc >= 8; zc /= 2) {
+            out->push_back({PATH_FUSED, sh[0], sh[1], zc});
+            if (zc <= m / 8) break;
+        }
+    }
+    out->push_back({PATH_STAGED, 16, 8, m});
+}
+
+static std::string tune_key(int dtype, int m, int count)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    char k[96];
+    std::snprintf(k, sizeof k, "n=%d dtype=%d count=%d sms=%d", m, dtype, count, sms);
+    return k;
+}
+
+// Cache lines: {"key": "...", "shape": [path, tx, ty, zc], "ms": t}
+static bool cache_lookup(const char *path, const std::string &key, int *sh)
+{
+    if (!path) return false;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof line, f)) {
+        const std::string l(line);
+        if (l.find("\"" + key + "\"") == std::string::npos) continue;
+        const size_t p = l.find("\"shape\": [");
+        if (p == std::string::npos) continue;
+        if (std::sscanf(l.c_str() + p + 10, "%d, %d, %d, %d", &sh[0], &sh[1], &sh[2], &sh[3]) == 4) found = true;
+    }
+    std::fclose(f);
+    return found;
+}
+
+static void cache_store(const char *path, const std::string &key, const int *sh, double ms)
+{
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "{\"key\": \"%s\", \"shape\": [%d, %d, %d, %d], \"ms\": %.6f}\n", key.c_str(),
+                 sh[0], sh[1], sh[2], sh[3], ms);
+    std::fclose(f);
+}
+
+template <typename T>
+static parareal_status tune_one(parareal_ctx *c, const char *cache, int m, int count, double dt,
+                                int *path, int *tx, int *ty, int *zc, double *best_ms)
+{
+    const int dtype = c->f64 ? PARAREAL_F64 : PARAREAL_F32;
+    const std::string key = tune_key(dtype, m, count);
+    int sh[4];
+    if (cache_lookup(cache, key, sh) &&
+        (sh[0] == PATH_STAGED || rk4_fused_supported(dtype, m, sh[1], sh[2]))) {
+        *path = sh[0]; *tx = sh[1]; *ty = sh[2]; *zc = sh[3];
+        *best_ms = -1.0;
+        return PARAREAL_OK;
+    }
+    std::vector<std::array<int, 4>> cand;
+    candidates(dtype, m, &cand);
+    double best = 1e30;
+    std::array<int, 4> pick = cand.back();
+    for (auto &k : cand) {
+        double ms;
+        parareal_status s = time_shape<T>(c, m, count, k[0], k[1], k[2], k[3], dt, &ms);
+        if (s != PARAREAL_OK) return s;
+        if (ms < best) { best = ms; pick = k; }
+    }
+    *path = pick[0]; *tx = pick[1]; *ty = pick[2]; *zc = pick[3];
+    *best_ms = best;
+    const int store[4] = {pick[0], pick[1], pick[2], pick[3]};
+    cache_store(cache, key, store, best);
+    return PARAREAL_OK;
+}
+
+extern "C" parareal_status parareal_autotune(parareal_ctx *c, const char *cache_path, double *ms2)
+{
+    if (!c) return PARAREAL_E_INVALID;
+    CK(cudaMemsetAsync(c->wC, 0, (size_t)c->N * c->P * c->esz, c->st));
+    CK(cudaMemsetAsync(c->cA, 0, (size_t)(c->r > 1 ? c->Pc : c->P) * c->esz, c->st));
+    double fms = 0.0, cms = 0.0;
+    parareal_status s;
+    if (c->f64)
+        s = tune_one<double>(c, cache_path, c->n, c->N, c->cfg.dt_fine, &c->fine_path, &c->fine_tx,
+                             &c->fine_ty, &c->fine_zc, &fms);
+    else
+        s = tune_one<float>(c, cache_path, c->n, c->N, c->cfg.dt_fine, &c->fine_path, &c->fine_tx,
+                            &c->fine_ty, &c->fine_zc, &fms);
+    if (s != PARAREAL_OK) return s;
+    if (c->cfg.coarse_kind == PARAREAL_COARSE_STENCIL && c->nc >= 8) {
+        // the coarse sweep runs one field at a time on the coarse grid
+        void *saveC = c->wC;
+        c->wC = c->cA;   // input of the timed coarse steps
+        if (c->f64)
+            s = tune_one<double>(c, cache_path, c->nc, 1, c->cfg.dt_coarse, &c->coarse_path,
+                                 &c->coarse_tx, &c->coarse_ty, &c->coarse_zc, &cms);
+        else
+            s = tune_one<float>(c, cache_path, c->nc, 1, c->cfg.dt_coarse, &c->coarse_path,
+                                &c->coarse_tx, &c->coarse_ty, &c->coarse_zc, &cms);
+        c->wC = saveC;
+        if (s != PARAREAL_OK) return s;
+    }
+    if (ms2) { ms2[0] = fms; ms2[1] = cms; }
+    c->has_problem = false;   // the iterate was used as scratch
+    c->started = false;
+    return PARAREAL_OK;
+}
+
+extern "C" parareal_status parareal_get_launch_shape(const parareal_ctx *c, int *fine4, int *coarse4)
+{
+    if (!c) return PARAREAL_E_INVALID;
+    if (fine4) { fine4[0] = c->fine_path; fine4[1] = c->fine_tx; fine4[2] = c->fine_ty; fine4[3] = c->fine_zc; }
+    if (coarse4) { coarse4[0] = c->coarse_path; coarse4[1] = c->coarse_tx; coarse4[2] = c->coarse_ty; coarse4[3] = c->coarse_zc; }
+    return PARAREAL_OK;
 }

@@ -52,6 +52,7 @@ template <typename T>
 cudaError_t launch_rk4_fused(const StepArgs &a, const T *in, T *out, int tile_x, int tile_y,
                              int zchunk, cudaStream_t st);
 bool rk4_fused_supported(int dtype, int n, int tile_x, int tile_y);
+cudaError_t configure_rk4_kernels();
 
 // One RK4 stage per launch (no halo recomputation; state kept in HBM/L2).
 template <typename T>

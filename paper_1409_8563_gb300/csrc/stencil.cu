@@ -291,20 +291,20 @@ static cudaError_t launch_fused_shape(const StepArgs &a, const T *in, T *out, in
                                       cudaStream_t st)
 {
     using S = FusedShape<T, TX, TY>;
-    static bool configured = false;   // per template instance, per process
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(rk4_fused_kernel<T, TX, TY>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)S::SMEM);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
     const int tiles_x = a.n / TX, tiles_y = a.n / TY;
     const int nzc = (a.n + zchunk - 1) / zchunk;
     const long long blocks = (long long)a.count * tiles_x * tiles_y * nzc;
     rk4_fused_kernel<T, TX, TY><<<(unsigned)blocks, S::NT, S::SMEM, st>>>(a, in, out, tiles_x,
                                                                          tiles_y, zchunk, nzc);
     return cudaGetLastError();
+}
+
+template <typename T, int TX, int TY>
+static cudaError_t configure_shape()
+{
+    return cudaFuncSetAttribute(rk4_fused_kernel<T, TX, TY>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)FusedShape<T, TX, TY>::SMEM);
 }
 
 // Tile shapes compiled for the fused kernel.
@@ -317,6 +317,18 @@ static cudaError_t launch_fused_shape(const StepArgs &a, const T *in, T *out, in
     X(double, 32, 8)       \
     X(double, 16, 16)      \
     X(double, 16, 8)
+
+// Shared-memory opt-in of every compiled shape (once per device, before any
+// launch or stream capture).
+cudaError_t configure_rk4_kernels()
+{
+    cudaError_t e = cudaSuccess;
+#define PR_CONF(T, TX, TY) \
+    if (e == cudaSuccess) e = configure_shape<T, TX, TY>();
+    PR_FUSED_SHAPES(PR_CONF)
+#undef PR_CONF
+    return e;
+}
 
 bool rk4_fused_supported(int dtype, int n, int tile_x, int tile_y)
 {

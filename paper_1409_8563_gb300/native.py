@@ -85,6 +85,17 @@ SIGNATURES = {
     "parareal_make_pairs": (_i, [_vp, _vp, _i, _vp, _vp, _ip]),
     "parareal_train_coarse": (_i, [_vp, _vp, _vp, _ip, _i, _vp, _dp]),
     "parareal_coarse_model_grad": (_i, [_vp, _vp, _vp, _ip, _i, _vp, _dp]),
+    "parareal_autotune": (_i, [_vp, _cp, _dp]),
+    "parareal_get_launch_shape": (_i, [_vp, _ip, _ip]),
+    "parareal_batch_create": (_i, [ctypes.POINTER(Config), _i, _vp, ctypes.POINTER(_vp)]),
+    "parareal_batch_set_problem": (_i, [_vp, _i, _vp, _i, _i]),
+    "parareal_batch_serial_fine": (_i, [_vp, _i]),
+    "parareal_batch_iterate": (_i, [_vp, _i, _d, _i, _ip, _dp]),
+    "parareal_batch_autotune": (_i, [_vp, _cp]),
+    "parareal_batch_context": (_vp, [_vp, _i]),
+    "parareal_batch_graph_launches": (ctypes.c_longlong, [_vp]),
+    "parareal_batch_last_error": (_cp, [_vp]),
+    "parareal_batch_destroy": (None, [_vp]),
     "parareal_profile": (_i, [_vp, _i]),
     "parareal_profile_read": (_i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]),
     "parareal_launch_count": (ctypes.c_longlong, [_vp]),
@@ -250,6 +261,18 @@ class Parareal:
                                                      ctypes.byref(loss)))
         return loss.value
 
+    def autotune(self, cache_path=None):
+        """Time the launch shapes and keep the fastest (call before set_problem)."""
+        ms = (ctypes.c_double * 2)()
+        cp = cache_path.encode() if cache_path else None
+        self._check(lib().parareal_autotune(self._h, cp, ms))
+        return ms[0], ms[1]
+
+    def launch_shape(self):
+        f, c = (ctypes.c_int * 4)(), (ctypes.c_int * 4)()
+        self._check(lib().parareal_get_launch_shape(self._h, f, c))
+        return tuple(f[:]), tuple(c[:])
+
     def profile(self, enable=True):
         return self._check(lib().parareal_profile(self._h, int(enable)))
 
@@ -279,3 +302,68 @@ class Parareal:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class _View(Parareal):
+    """A context owned by a Batch (not destroyed by this object)."""
+
+    def __init__(self, handle, cfg):  # noqa: D401 - no parareal_create here
+        self.cfg = cfg
+        self.status = OK
+        self._h = ctypes.c_void_p(handle)
+
+    def close(self):
+        self._h = None
+
+
+class Batch:
+    """Independent problems of uneven sizes advanced together (parareal_batch_*)."""
+
+    def __init__(self, cfgs, stream=None):
+        self.cfgs = list(cfgs)
+        arr = (Config * len(self.cfgs))(*self.cfgs)
+        h = ctypes.c_void_p()
+        st = lib().parareal_batch_create(arr, len(self.cfgs), _stream_ptr(stream), ctypes.byref(h))
+        if st < 0:
+            raise PararealError(st, lib().parareal_last_error(None).decode())
+        self._h = h
+
+    def _check(self, st):
+        if st < 0:
+            raise PararealError(st, lib().parareal_batch_last_error(self._h).decode())
+        return st
+
+    def context(self, i):
+        return _View(lib().parareal_batch_context(self._h, i), self.cfgs[i])
+
+    def set_problem(self, i, u0):
+        p, code, mem, _k = _field(u0)
+        return self._check(lib().parareal_batch_set_problem(self._h, i, p, code, mem))
+
+    def serial_fine(self, as_reference=True):
+        return self._check(lib().parareal_batch_serial_fine(self._h, int(as_reference)))
+
+    def iterate(self, k_max, tol=0.0, stop_rule=STOP_NONE):
+        M = len(self.cfgs)
+        k = (ctypes.c_int * M)()
+        d = (ctypes.c_double * M)()
+        self._check(lib().parareal_batch_iterate(self._h, k_max, tol, stop_rule, k, d))
+        return np.array(k[:]), np.array(d[:])
+
+    def autotune(self, cache_path=None):
+        cp = cache_path.encode() if cache_path else None
+        return self._check(lib().parareal_batch_autotune(self._h, cp))
+
+    def graph_launches(self):
+        return int(lib().parareal_batch_graph_launches(self._h))
+
+    def close(self):
+        if self._h:
+            lib().parareal_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
