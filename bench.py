@@ -327,6 +327,146 @@ def run(args):
     return 0
 
 
+# ------------------------------------------------- the other configurations
+
+def _timed(fn, reps=1):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = None
+    for _ in range(reps):
+        out = fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) * 1000 / reps, out
+
+
+def run_fp64_32(args):
+    """32^3 FP64, N = 8: time-to-1e-6 Parareal vs serial fine."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1409_8563_gb300 import configs, native
+    cfg, u0 = configs.plain_fp64_32()
+    ctx = native.Parareal(cfg)
+    u = torch.from_numpy(u0).cuda()
+    ctx.set_problem(u)
+    ctx.serial_fine(None, as_reference=True)
+    serial_ms, _ = _timed(lambda: ctx.serial_fine(None, as_reference=True), 3)
+
+    def solve():
+        ctx.set_problem(u)
+        return ctx.iterate(cfg.n_slices, TOL, native.STOP_DEFECT)
+    for _ in range(args.warmup):
+        solve()
+    ms, (k, h) = _timed(solve, args.steps)
+    P, N, nf = 32 ** 3, cfg.n_slices, round(cfg.T / cfg.n_slices / cfg.dt_fine)
+    ups = sum(N - j for j in range(k)) * P * nf
+    print(json.dumps({"workload": "fp64_32", "time_to_1e-6_ms": ms, "serial_fine_ms": serial_ms,
+                      "parareal_over_serial": ms / serial_ms, "k_star": k,
+                      "defects": [float(x) for x in h[:, 2]], "glups_in_solve": ups / ms / 1e6,
+                      "dtype": "f64", "steps": args.steps, "warmup": args.warmup}))
+    ctx.close()
+    return 0
+
+
+def run_learned_128(args):
+    """128^3, N = 32: learned coarse propagator (trained here on pairs the
+    fine solver generates) vs stencil coarse propagator vs shift only vs
+    serial fine: iterations and time to d^k <= 1e-6."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1409_8563_gb300 import configs, inputs, native
+    base, u0 = configs.fp32_128()
+    n, N = base.n, base.n_slices
+    mk = lambda kind, r, dtg: native.Config.make(n, N, base.T, base.dt_fine, dtg, r,
+                                                 fine_dtype=native.F32, coarse_kind=kind,
+                                                 nu0=base.nu0, nu_amp=base.nu_amp,
+                                                 nu_omega=base.nu_omega)
+    learned = native.Parareal(mk(native.COARSE_LEARNED, 1, base.T / N))
+    n_ics = args.n_ics
+    t0 = time.perf_counter()
+    ics = torch.stack([torch.from_numpy(inputs.spectral_ic(n, seed=1000 + i, kmax=32)).float()
+                       for i in range(n_ics)]).cuda()
+    pu = torch.empty((n_ics * N, n, n, n), dtype=torch.float32, device="cuda")
+    pf = torch.empty_like(pu)
+    sl = learned.make_pairs(ics, pu, pf)
+    torch.cuda.synchronize()
+    pairs_s = time.perf_counter() - t0
+    del ics
+    learned.set_coarse_model(inputs.initial_weights(seed=0))
+    t0 = time.perf_counter()
+    hist = learned.train_coarse(pu, pf, sl, epochs=args.epochs, batch=args.batch, lr=args.lr, seed=1)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del pu, pf
+    torch.cuda.empty_cache()
+    u = torch.from_numpy(u0).cuda()
+    res = {}
+    ctxs = {"learned": learned,
+            "stencil": native.Parareal(base),
+            "shift": native.Parareal(mk(native.COARSE_SHIFT, 1, base.T / N))}
+    serial_ms = None
+    for name, c in ctxs.items():
+        c.set_problem(u)
+        c.serial_fine(None, as_reference=True)
+        if serial_ms is None:
+            serial_ms, _ = _timed(lambda: c.serial_fine(None, as_reference=True), 2)
+
+        def solve(c=c):
+            c.set_problem(u)
+            return c.iterate(N, TOL, native.STOP_DEFECT)
+        solve()
+        ms, (k, h) = _timed(solve, args.steps)
+        res[name] = {"k_star": k, "time_to_1e-6_ms": ms, "defects": [float(x) for x in h[:, 2]]}
+    print(json.dumps({"workload": "learned_128", "serial_fine_ms": serial_ms, "runs": res,
+                      "train": {"pairs": int(len(sl)), "epochs": args.epochs, "batch": args.batch,
+                                "lr": args.lr, "loss": [float(x) for x in hist],
+                                "pairs_s": pairs_s, "train_s": train_s}}))
+    for c in ctxs.values():
+        c.close()
+    return 0
+
+
+def run_batch64(args):
+    """64 uneven instances (sizes from {32,48,64,96,128}, nu0 in [0.002, 0.02],
+    N = 8, T = 1): one CUDA graph per round; autotuned launch shapes."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1409_8563_gb300 import configs, inputs, native
+    ns, nus = inputs.batch_instances(seed=0)
+    cfgs, u0s = [], []
+    for i, (n, nu0) in enumerate(zip(ns, nus)):
+        cfg, u0 = configs.batch_instance(n, nu0, seed=i)
+        cfgs.append(cfg)
+        u0s.append(torch.from_numpy(u0).cuda())
+    b = native.Batch(cfgs)
+    tune_ms, _ = _timed(lambda: b.autotune(os.path.join(ROOT, "paper_1409_8563_gb300", "tune_cache.jsonl")))
+    for i, u in enumerate(u0s):
+        b.set_problem(i, u)
+    b.serial_fine(True)
+    serial_ms, _ = _timed(lambda: b.serial_fine(True), 1)
+
+    def solve():
+        for i, u in enumerate(u0s):
+            b.set_problem(i, u)
+        return b.iterate(8, TOL, native.STOP_DEFECT)
+    solve()
+    ms, (k, d) = _timed(solve, args.steps)
+    ups = 0
+    for cfg, kk in zip(cfgs, k):
+        nf = round(cfg.T / cfg.n_slices / cfg.dt_fine)
+        ups += sum(cfg.n_slices - j for j in range(int(kk))) * cfg.n ** 3 * nf
+    print(json.dumps({"workload": "batch64", "time_to_1e-6_ms": ms, "serial_fine_ms": serial_ms,
+                      "k_star": [int(x) for x in k], "max_defect": float(max(d)),
+                      "glups_in_solve": ups / ms / 1e6, "autotune_ms": tune_ms,
+                      "graph_launches": b.graph_launches()}))
+    b.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,9 +475,21 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="fp32_256",
+                    choices=["fp32_256", "fp64_32", "learned_128", "batch64"])
+    ap.add_argument("--n-ics", type=int, default=63)
+    ap.add_argument("--epochs", type=int, default=10)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=1e-3)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "fp64_32":
+        return run_fp64_32(args)
+    if args.workload == "learned_128":
+        return run_learned_128(args)
+    if args.workload == "batch64":
+        return run_batch64(args)
     return run(args)
 
 

@@ -18,11 +18,13 @@
  * - Fields are n^3 arrays, x fastest: index (z*n + y)*n + x, point x_i = i/n.
  * - A pointer argument is a device pointer when the accompanying `mem`
  *   argument is PARAREAL_MEM_DEVICE and a host pointer when it is
- *   PARAREAL_MEM_HOST.  Host buffers are copied with cudaMemcpyAsync on the
- *   context stream and the call synchronises that stream before returning.
- * - Caller-supplied buffers are borrowed for the duration of the call only;
- *   the context owns all of its device workspace and frees it in
- *   parareal_destroy.
+ *   PARAREAL_MEM_HOST.  Buffers are copied with cudaMemcpyAsync on the
+ *   context stream.
+ * - Caller-supplied buffers are borrowed for the duration of the call only:
+ *   every call that reads or writes one synchronises the context stream
+ *   before it returns (except parareal_diff_norms_noalloc, which is fully
+ *   asynchronous).  The context owns all of its device workspace and frees it
+ *   in parareal_destroy.
  * - Device work is ordered on the context stream (the stream passed to
  *   parareal_create; NULL = the legacy default stream).  Calls that return
  *   host scalars synchronise that stream.
@@ -237,6 +239,9 @@ parareal_status parareal_get_launch_shape(const parareal_ctx *ctx, int *fine4, i
  * stopped) is one CUDA graph whose parallel branches are the instances.
  * There is no counterpart in the paper, which runs one problem. */
 typedef struct parareal_batch parareal_batch;
+/* cuda_stream: the stream rounds are captured on and launched in (NULL: the
+ * batch creates a stream of its own; the legacy default stream cannot be
+ * captured). */
 parareal_status parareal_batch_create(const parareal_config *cfgs, int count, void *cuda_stream,
                                       parareal_batch **out);
 parareal_status parareal_batch_set_problem(parareal_batch *b, int i, const void *u0, int dtype, int mem);

@@ -547,7 +547,7 @@ static parareal_status load_field(parareal_ctx *c, double *dst, const void *src,
         CK(cudaMemcpyAsync(stage, src, bytes, kind, c->st));
         LK(launch_convert_f32_to_f64(stage, dst, c->P, c->st));
     }
-    if (mem == PARAREAL_MEM_HOST) CK(cudaStreamSynchronize(c->st));
+    CK(cudaStreamSynchronize(c->st));   // the caller's buffer is borrowed for this call only
     return PARAREAL_OK;
 }
 
@@ -564,7 +564,7 @@ static parareal_status store_field(parareal_ctx *c, void *dst, const double *src
         LK(launch_convert_f64_to_f32(src, stage, c->P, c->st));
         CK(cudaMemcpyAsync(dst, stage, (size_t)c->P * 4, kind, c->st));
     }
-    if (mem == PARAREAL_MEM_HOST) CK(cudaStreamSynchronize(c->st));
+    CK(cudaStreamSynchronize(c->st));   // the caller's buffer is borrowed for this call only
     return PARAREAL_OK;
 }
 
@@ -749,13 +749,13 @@ extern "C" parareal_status parareal_serial_fine(parareal_ctx *c, void *dst, int 
         if (dtype == PARAREAL_F64) {
             CK(cudaMemcpyAsync(dst, c->tmpd, P * 8, mem == PARAREAL_MEM_HOST ? cudaMemcpyDeviceToHost
                                                                              : cudaMemcpyDeviceToDevice, c->st));
-            if (mem == PARAREAL_MEM_HOST) CK(cudaStreamSynchronize(c->st));
+            CK(cudaStreamSynchronize(c->st));
         } else {
             float *stage = static_cast<float *>(c->wA);
             LK(launch_convert_f64_to_f32(c->tmpd, stage, P, c->st));
             CK(cudaMemcpyAsync(dst, stage, P * 4, mem == PARAREAL_MEM_HOST ? cudaMemcpyDeviceToHost
                                                                           : cudaMemcpyDeviceToDevice, c->st));
-            if (mem == PARAREAL_MEM_HOST) CK(cudaStreamSynchronize(c->st));
+            CK(cudaStreamSynchronize(c->st));
         }
     }
     return PARAREAL_OK;
@@ -815,6 +815,7 @@ static parareal_status propagate_t(parareal_ctx *c, int which, const void *src, 
             LK(launch_convert_f64_to_f32(res64, reinterpret_cast<float *>(dp), P, c->st));
         }
     }
+    CK(cudaStreamSynchronize(c->st));   // src and dst are borrowed for this call only
     return PARAREAL_OK;
 }
 

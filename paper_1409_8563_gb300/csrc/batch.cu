@@ -20,6 +20,7 @@ struct parareal_batch {
     std::vector<cudaEvent_t> join;
     cudaEvent_t fork = nullptr;
     cudaStream_t main = nullptr;
+    bool own_main = false;        // the legacy default stream cannot be captured
     std::vector<int> stopped;
     std::string err;
     long long graph_launches = 0;
@@ -45,6 +46,7 @@ extern "C" void parareal_batch_destroy(parareal_batch *b)
     for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->join) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->own_main && b->main) cudaStreamDestroy(b->main);
     delete b;
 }
 
@@ -55,6 +57,14 @@ extern "C" parareal_status parareal_batch_create(const parareal_config *cfgs, in
     *out = nullptr;
     parareal_batch *b = new parareal_batch();
     b->main = static_cast<cudaStream_t>(stream);
+    if (!b->main) {
+        if (cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) != cudaSuccess) {
+            b->main = nullptr;
+            parareal_batch_destroy(b);
+            return PARAREAL_E_CUDA;
+        }
+        b->own_main = true;
+    }
     if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
         parareal_batch_destroy(b);
         return PARAREAL_E_CUDA;

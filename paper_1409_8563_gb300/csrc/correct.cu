@@ -80,7 +80,7 @@ __device__ void block_reduce_store(Partial p, double *out)
 template <typename TP>
 __device__ __forceinline__ void lin_weights(int i, int r, int nc, int &lo, int &hi, TP &w)
 {
-    const TP s = ((TP)i - (TP)0.5 * (TP)(r - 1)) / (TP)r;
+    const TP s = ((TP)i - (TP)0.5 * (TP)(r - 1)) * ((TP)1 / (TP)r);
     const TP f = floor(s);
     w = s - f;
     lo = (int)f;
@@ -89,50 +89,65 @@ __device__ __forceinline__ void lin_weights(int i, int r, int nc, int &lo, int &
     hi = hi >= nc ? hi - nc : hi;
 }
 
+// Work is handed out in groups of R = max(1, RED_THREADS / n) rows of n
+// points: thread t owns x = t % n of row (t / n) of each group, so x and its
+// prolongation weights stay fixed per thread and no point index is divided.
 template <typename TF, typename TG>
 __global__ void __launch_bounds__(RED_THREADS)
 correct_kernel(const TF *__restrict__ Fv, const TG *__restrict__ gnew, const TG *__restrict__ gold,
                double *__restrict__ U, int n, int r, double *__restrict__ partials)
 {
-    const long long P = (long long)n * n * n;
     Partial acc{0ull, 0ull, 0.0, 0.0, 0};
     const int nc = n / r;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P;
-         p += (long long)gridDim.x * blockDim.x) {
-        double dg = 0.0;
-        if (r == 1) {
-            dg = (double)gnew[p] - (gold ? (double)gold[p] : 0.0);
-        } else {
-            // G's output change on the fine grid: trilinear prolongation of
-            // the difference of the two coarse results (exact in FP64, then
-            // rounded to the coarse precision TG).
-            const int x = (int)(p % n), y = (int)((p / n) % n), z = (int)(p / ((long long)n * n));
-            int x0, x1, y0, y1, z0, z1;
-            TG wx, wy, wz;
-            lin_weights<TG>(x, r, nc, x0, x1, wx);
-            lin_weights<TG>(y, r, nc, y0, y1, wy);
-            lin_weights<TG>(z, r, nc, z0, z1, wz);
-            auto dc = [&](int I, int J, int K) {
-                const long long q = ((long long)K * nc + J) * nc + I;
-                return (TG)((double)gnew[q] - (gold ? (double)gold[q] : 0.0));
-            };
-            const TG c00 = fma(wx, dc(x1, y0, z0) - dc(x0, y0, z0), dc(x0, y0, z0));
-            const TG c10 = fma(wx, dc(x1, y1, z0) - dc(x0, y1, z0), dc(x0, y1, z0));
-            const TG c01 = fma(wx, dc(x1, y0, z1) - dc(x0, y0, z1), dc(x0, y0, z1));
-            const TG c11 = fma(wx, dc(x1, y1, z1) - dc(x0, y1, z1), dc(x0, y1, z1));
-            const TG c0 = fma(wy, c10 - c00, c00);
-            const TG c1 = fma(wy, c11 - c01, c01);
-            dg = (double)fma(wz, c1 - c0, c0);
+    const int R = n >= (int)blockDim.x ? 1 : (int)blockDim.x / n;   // rows per group
+    const int lanes = R * n;
+    const long long rows = (long long)n * n;
+    for (int xs = threadIdx.x % n; xs < n; xs += blockDim.x) {
+        if (threadIdx.x >= lanes && n < (int)blockDim.x) break;
+        const int x = n >= (int)blockDim.x ? xs : (int)threadIdx.x % n;
+        const int rsub = n >= (int)blockDim.x ? 0 : (int)threadIdx.x / n;
+        int x0 = 0, x1 = 0;
+        TG wx = (TG)0;
+        if (r > 1) lin_weights<TG>(x, r, nc, x0, x1, wx);
+        for (long long g = blockIdx.x; g * R < rows; g += gridDim.x) {
+            const long long row = g * R + rsub;
+            if (row >= rows) break;
+            const long long p = row * n + x;
+            double dg = 0.0;
+            if (r == 1) {
+                dg = (double)gnew[p] - (gold ? (double)gold[p] : 0.0);
+            } else {
+                // G's output change on the fine grid: trilinear prolongation
+                // of the difference of the two coarse results (exact in FP64,
+                // then rounded to the coarse precision TG)
+                const int z = (int)(row / n), y = (int)(row - (long long)z * n);
+                int y0, y1, z0, z1;
+                TG wy, wz;
+                lin_weights<TG>(y, r, nc, y0, y1, wy);
+                lin_weights<TG>(z, r, nc, z0, z1, wz);
+                auto dc = [&](int I, int J, int K) {
+                    const long long q = ((long long)K * nc + J) * nc + I;
+                    return (TG)((double)gnew[q] - (gold ? (double)gold[q] : 0.0));
+                };
+                const TG c00 = fma(wx, dc(x1, y0, z0) - dc(x0, y0, z0), dc(x0, y0, z0));
+                const TG c10 = fma(wx, dc(x1, y1, z0) - dc(x0, y1, z0), dc(x0, y1, z0));
+                const TG c01 = fma(wx, dc(x1, y0, z1) - dc(x0, y0, z1), dc(x0, y0, z1));
+                const TG c11 = fma(wx, dc(x1, y1, z1) - dc(x0, y1, z1), dc(x0, y1, z1));
+                const TG c0 = fma(wy, c10 - c00, c00);
+                const TG c1 = fma(wy, c11 - c01, c01);
+                dg = (double)fma(wz, c1 - c0, c0);
+            }
+            const double un = (Fv ? (double)Fv[p] : 0.0) + dg;
+            const double du = un - U[p];
+            U[p] = un;
+            const unsigned long long bu = abs_bits(un), bd = abs_bits(du);
+            acc.bad |= nonfinite_bits(bu) ? 1 : 0;
+            acc.mx_u = bu > acc.mx_u ? bu : acc.mx_u;
+            acc.mx_d = bd > acc.mx_d ? bd : acc.mx_d;
+            acc.s_d = fma(du, du, acc.s_d);
+            acc.s_u = fma(un, un, acc.s_u);
         }
-        const double un = (Fv ? (double)Fv[p] : 0.0) + dg;
-        const double du = un - U[p];
-        U[p] = un;
-        const unsigned long long bu = abs_bits(un), bd = abs_bits(du);
-        acc.bad |= nonfinite_bits(bu) ? 1 : 0;
-        acc.mx_u = bu > acc.mx_u ? bu : acc.mx_u;
-        acc.mx_d = bd > acc.mx_d ? bd : acc.mx_d;
-        acc.s_d = fma(du, du, acc.s_d);
-        acc.s_u = fma(un, un, acc.s_u);
+        if (n < (int)blockDim.x) break;
     }
     block_reduce_store(acc, partials + 5ll * blockIdx.x);
 }

@@ -84,25 +84,57 @@ __device__ __forceinline__ double nu_at(const StepArgs &a, double t)
     return a.nu0 * (1.0 + a.nu_amp * sin(a.nu_omega * t));
 }
 
-// delta[i] = sum of the 7 weighted neighbours of point i of this thread's
-// vector.  c / zm / zp: this column at planes p, p-1, p+1 (registers);
-// the x and y neighbours come from the shared-memory plane Sp ([RY][RX]).
-template <typename T, int RX, int RY>
-__device__ __forceinline__ void stage_delta(T (&d)[VecT<T>::V], const T *__restrict__ Sp, int qx,
-                                            int ry, const T (&c)[VecT<T>::V],
-                                            const T (&zm)[VecT<T>::V],
+template <typename T, int TX, int TY>
+struct FusedShape {
+    static constexpr int V = VecT<T>::V;
+    static constexpr int RX = TX + 8;          // region width incl. 4-point halo per side
+    static constexpr int RY = TY + 8;
+    static constexpr int QX = RX / V;          // vectors per region row
+    static constexpr int NT = QX * RY;         // threads per CTA
+    static constexpr int PL = RX * RY;         // values per shared plane
+    static constexpr int EL = QX * RY;         // entries per edge array
+    static constexpr int D = 4;                // planes of u in flight ahead of use
+    static constexpr int RING = 6;             // u planes resident (divides the unroll of 12)
+    // u ring [RING][PL], stage planes [2][3][PL], u edges [RING][2][EL], stage edges [2][3][2][EL]
+    static constexpr size_t SMEM = ((size_t)(RING + 6) * PL + (size_t)(2 * RING + 12) * EL) * sizeof(T);
+};
+
+// 16-byte asynchronous global->shared copy (L2 only, bypassing L1) and its
+// group bookkeeping.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Per-thread constants of the fused kernel: shared-memory offsets of the own
+// vector, of the vectors one row up/down (y neighbours) and of the edge
+// entries of the vectors to the left/right (x neighbours).  At the region
+// border the offsets are clamped in bounds; the values read there only feed
+// halo points that never reach an output.
+struct FusedLane {
+    int own, ym, yp, eo, el, er;
+};
+
+// delta[i] = dt * A(nu_s) y at the V points of this thread's vector: c, zm,
+// zp are the vector at planes p, p-1, p+1 (registers); the y neighbours come
+// from the shared plane Sp, the x neighbours from its edge arrays
+// (E[1] = last element of each vector, E[0] = first element).
+template <typename T>
+__device__ __forceinline__ void stage_delta(T (&d)[VecT<T>::V], const T *__restrict__ Sp,
+                                            const T *__restrict__ E, int EL, const FusedLane &L,
+                                            const T (&c)[VecT<T>::V], const T (&zm)[VecT<T>::V],
                                             const T (&zp)[VecT<T>::V], const T (&w)[7])
 {
     constexpr int V = VecT<T>::V;
-    const int rym = ry > 0 ? ry - 1 : 0;
-    const int ryp = ry < RY - 1 ? ry + 1 : RY - 1;
-    const int xl = qx * V > 0 ? qx * V - 1 : 0;
-    const int xr = qx * V + V < RX ? qx * V + V : RX - 1;
     T ym[V], yp[V];
-    ldv<T>(Sp + rym * RX + qx * V, ym);
-    ldv<T>(Sp + ryp * RX + qx * V, yp);
-    const T left = Sp[ry * RX + xl];
-    const T right = Sp[ry * RX + xr];
+    ldv<T>(Sp + L.ym, ym);
+    ldv<T>(Sp + L.yp, yp);
+    const T left = E[EL + L.el];
+    const T right = E[L.er];
 #pragma unroll
     for (int i = 0; i < V; ++i) {
         const T l = (i == 0) ? left : c[i - 1];
@@ -118,41 +150,137 @@ __device__ __forceinline__ void stage_delta(T (&d)[VecT<T>::V], const T *__restr
     }
 }
 
-template <typename T, int TX, int TY>
-struct FusedShape {
-    static constexpr int V = VecT<T>::V;
-    static constexpr int RX = TX + 8;          // region width incl. 4-point halo per side
-    static constexpr int RY = TY + 8;
-    static constexpr int QX = RX / V;          // vectors per region row
-    static constexpr int NT = QX * RY;         // threads per CTA
-    static constexpr int D = 4;                // planes of u in flight ahead of use
-    static constexpr int RING = D + 2;         // u planes resident: in flight + current + previous
-    static constexpr size_t SMEM = (size_t)(RING + 2 * 3) * RX * RY * sizeof(T);
+// Register windows of one thread, indexed by iteration modulo their period:
+// u of iteration j in U[j % 4], y2/y3/y4 produced at iteration j in
+// Y*[j % 3], the RK4 increment sum started at iteration j in A[j % 4].
+template <typename T>
+struct FusedRegs {
+    T U[4][VecT<T>::V];
+    T Y2[3][VecT<T>::V], Y3[3][VecT<T>::V], Y4[3][VecT<T>::V];
+    T A[4][VecT<T>::V];
 };
 
-// 16-byte asynchronous global->shared copy (L2 only, bypassing L1) and its
-// group bookkeeping.
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+// Everything one z-iteration needs besides the registers.
+template <typename T>
+struct FusedIter {
+    T *ring, *planes, *ering, *eplanes;   // shared memory
+    const T *src;                          // global: this thread's column, plane 0
+    T *dst;
+    long long plane;                       // n*n
+    int n, n_it, zreq;                     // iterations, wrapped plane of the next request
+    long long ooff;                        // output offset of the current iteration
+    bool act1, act2, act3, act4, owner;
+};
 
+// One z-iteration at compile-time phase PH = it % 12 (see the kernel).
+template <typename T, int TX, int TY, int PH>
+__device__ __forceinline__ void fused_step(FusedIter<T> &I, FusedRegs<T> &R, const FusedLane &L,
+                                           int it, const T (&w1)[7], const T (&w2)[7],
+                                           const T (&w4)[7])
+{
+    using S = FusedShape<T, TX, TY>;
+    constexpr int V = S::V, PL = S::PL, EL = S::EL, D = S::D, RING = S::RING;
+    constexpr T c6 = (T)(1.0 / 6.0), c3 = (T)(1.0 / 3.0), hf = (T)0.5;
+    if (it >= I.n_it) return;
+    // request the u plane of iteration it + D
+    if (it + D < I.n_it)
+        cp_async16(I.ring + ((PH + D) % RING) * PL + L.own, I.src + (long long)I.zreq * I.plane);
+    cp_async_commit();
+    I.zreq = I.zreq + 1 == I.n ? 0 : I.zreq + 1;
+    cp_async_wait<D>();
+    T un[V];
+    ldv<T>(I.ring + (PH % RING) * PL + L.own, un);
+    // edges of u(it) for the x neighbours of stage 1 in the next iteration
+    T *eu = I.ering + (PH % RING) * 2 * EL;
+    eu[L.eo] = un[0];
+    eu[EL + L.eo] = un[V - 1];
+
+    const T *Su = I.ring + ((PH + RING - 1) % RING) * PL;
+    const T *Eu = I.ering + ((PH + RING - 1) % RING) * 2 * EL;
+    const T *Sc = I.planes + (PH & 1) * 3 * PL;
+    const T *Ec = I.eplanes + (PH & 1) * 6 * EL;
+    T *Sn = I.planes + ((PH + 1) & 1) * 3 * PL;
+    T *En = I.eplanes + ((PH + 1) & 1) * 6 * EL;
+
+    T d[V];
+    T y2n[V] = {}, y3n[V] = {}, y4n[V] = {}, accn[V] = {};
+    // stage 1 at the plane of iteration it-1
+    if (I.act1) {
+        stage_delta<T>(d, Su, Eu, EL, L, R.U[(PH + 3) % 4], R.U[(PH + 2) % 4], un, w1);
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            y2n[i] = fma(hf, d[i], R.U[(PH + 3) % 4][i]);
+            accn[i] = c6 * d[i];
+        }
+    }
+    // stage 2 at the plane of iteration it-2
+    if (I.act2) {
+        stage_delta<T>(d, Sc, Ec, EL, L, R.Y2[(PH + 2) % 3], R.Y2[(PH + 1) % 3], y2n, w2);
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            y3n[i] = fma(hf, d[i], R.U[(PH + 2) % 4][i]);
+            R.A[(PH + 3) % 4][i] = fma(c3, d[i], R.A[(PH + 3) % 4][i]);
+        }
+    }
+    // stage 3 at the plane of iteration it-3
+    if (I.act3) {
+        stage_delta<T>(d, Sc + PL, Ec + 2 * EL, EL, L, R.Y3[(PH + 2) % 3], R.Y3[(PH + 1) % 3], y3n, w2);
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            y4n[i] = R.U[(PH + 1) % 4][i] + d[i];
+            R.A[(PH + 2) % 4][i] = fma(c3, d[i], R.A[(PH + 2) % 4][i]);
+        }
+    }
+    // stage 4 at the plane of iteration it-4: the finished step
+    if (I.act4) {
+        stage_delta<T>(d, Sc + 2 * PL, Ec + 4 * EL, EL, L, R.Y4[(PH + 2) % 3], R.Y4[(PH + 1) % 3], y4n, w4);
+        if (I.owner && it >= 8) {
+            T o[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) o[i] = R.U[PH % 4][i] + fma(c6, d[i], R.A[(PH + 1) % 4][i]);
+            stv<T>(I.dst + I.ooff, o);
+        }
+    }
+    I.ooff += I.plane;
+    stv<T>(Sn + L.own, y2n);
+    stv<T>(Sn + PL + L.own, y3n);
+    stv<T>(Sn + 2 * PL + L.own, y4n);
+    En[L.eo] = y2n[0];
+    En[EL + L.eo] = y2n[V - 1];
+    En[2 * EL + L.eo] = y3n[0];
+    En[3 * EL + L.eo] = y3n[V - 1];
+    En[4 * EL + L.eo] = y4n[0];
+    En[5 * EL + L.eo] = y4n[V - 1];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        R.U[PH % 4][i] = un[i];
+        R.Y2[PH % 3][i] = y2n[i];
+        R.Y3[PH % 3][i] = y3n[i];
+        R.Y4[PH % 3][i] = y4n[i];
+        R.A[PH % 4][i] = accn[i];
+    }
+}
+
+// One RK4 step of `count` fields.  Each CTA owns a TX x TY column (plus a
+// 4-point halo in x and y) of one field and a z range [z_lo, z_hi); it runs
+// n_it = (z_hi - z_lo) + 8 iterations, iteration it loading plane
+// z_lo - 4 + it and finishing plane z_lo - 8 + it (stage s works on plane
+// z_lo - 4 + it - s).  The z loop is unrolled by 12, a multiple of every
+// register window's period, so the windows never move between registers.
 template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(FusedShape<T, TX, TY>::NT, 1)
 rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int tiles_x,
                  int tiles_y, int zchunk, int nzc)
 {
     using S = FusedShape<T, TX, TY>;
-    constexpr int V = S::V, RX = S::RX, RY = S::RY, QX = S::QX;
-    constexpr int PL = RX * RY;
+    constexpr int V = S::V, RX = S::RX, RY = S::RY, QX = S::QX, PL = S::PL, EL = S::EL;
     constexpr int D = S::D, RING = S::RING;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *ring = reinterpret_cast<T *>(smem_raw);     // [RING][RY][RX]   u planes
-    T *planes = ring + RING * PL;                  // [2][3][RY][RX]   y2, y3, y4 planes
+    T *ring = reinterpret_cast<T *>(smem_raw);
+    T *planes = ring + RING * PL;
+    T *ering = planes + 6 * PL;
+    T *eplanes = ering + 2 * RING * EL;
     __shared__ T s_w[3][7];                        // stage 1, stages 2-3, stage 4
 
     const int tid = threadIdx.x;
@@ -183,105 +311,71 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
         w4[k] = s_w[2][k];
     }
 
+    FusedLane L;
+    L.own = ry * RX + qx * V;
+    L.ym = (ry > 0 ? ry - 1 : 0) * RX + qx * V;
+    L.yp = (ry < RY - 1 ? ry + 1 : RY - 1) * RX + qx * V;
+    L.eo = ry * QX + qx;
+    L.el = ry * QX + (qx > 0 ? qx - 1 : 0);          // right edge of the left vector
+    L.er = ry * QX + (qx < QX - 1 ? qx + 1 : QX - 1); // left edge of the right vector
+
     const int gx = ((tx * TX - 4 + qx * V) % n + n) % n;
     const int gy = ((ty * TY - 4 + ry) % n + n) % n;
-    const long long plane = (long long)n * n;
-    const T *src = in + (long long)f * a.P + (long long)gy * n + gx;
-    T *dst = out + (long long)f * a.P + (long long)gy * n + gx;
-
+    FusedIter<T> I;
+    I.ring = ring;
+    I.planes = planes;
+    I.ering = ering;
+    I.eplanes = eplanes;
+    I.plane = (long long)n * n;
+    I.src = in + (long long)f * a.P + (long long)gy * n + gx;
+    I.dst = out + (long long)f * a.P + (long long)gy * n + gx;
+    I.n = n;
+    const int z_lo = zc * zchunk;
+    const int z_hi = min(z_lo + zchunk, n);
+    I.n_it = z_hi - z_lo + 8;
+    I.ooff = (long long)(z_lo - 8) * I.plane;
     // stage s is needed on rows [s, RY-s) and elements [s, RX-s) of the region
     auto active = [&](int s) {
         return ry >= s && ry < RY - s && (qx + 1) * V > s && qx * V < RX - s;
     };
-    const bool act1 = active(1), act2 = active(2), act3 = active(3), act4 = active(4);
-    const bool owner = ry >= 4 && ry < 4 + TY && qx * V >= 4 && qx * V < 4 + TX;
+    I.act1 = active(1);
+    I.act2 = active(2);
+    I.act3 = active(3);
+    I.act4 = active(4);
+    I.owner = ry >= 4 && ry < 4 + TY && qx * V >= 4 && qx * V < 4 + TX;
 
-    const int z_lo = zc * zchunk;
-    const int z_hi = min(z_lo + zchunk, n);
-
-    // register windows (index 0 = newest plane)
-    T U[4][V] = {}, Y2[2][V] = {}, Y3[2][V] = {}, Y4[2][V] = {}, A[3][V] = {};
-    constexpr T c6 = (T)(1.0 / 6.0), c3 = (T)(1.0 / 3.0), hf = (T)0.5;
-
-    // u plane z lives in ring slot (z - z_lo + 4) mod RING; plane zi + D is
-    // requested while plane zi is consumed, so DRAM latency overlaps D
-    // iterations of compute.
-    const int z_end = z_hi + 4;
-    const int my = ry * RX + qx * V;
-    // z >= z_lo - 5 everywhere below, so the offset keeps the index non-negative
-    auto slot = [&](int z) { return ring + ((z - z_lo + 4 + RING) % RING) * PL; };
-    auto request = [&](int z) {
-        if (z < z_end) {
-            const int zw = ((z % n) + n) % n;
-            cp_async16(slot(z) + my, src + (long long)zw * plane);
-        }
+    // prologue: planes of iterations 0 .. D-1 into ring slots 0 .. D-1
+    int z0 = z_lo - 4;
+    z0 = ((z0 % n) + n) % n;
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        if (q < I.n_it) cp_async16(ring + q * PL + L.own, I.src + (long long)z0 * I.plane);
         cp_async_commit();
-    };
-#pragma unroll
-    for (int q = 0; q < D; ++q) request(z_lo - 4 + q);
+        z0 = z0 + 1 == n ? 0 : z0 + 1;
+    }
+    I.zreq = z0;
 
-    int cur = 0;
-    for (int zi = z_lo - 4; zi < z_end; ++zi) {
-        request(zi + D);
-        cp_async_wait<D>();
-        T un[V];
-        ldv<T>(slot(zi) + my, un);
-        const T *Su = slot(zi - 1);                   // u at plane zi-1 (complete since last barrier)
-        const T *Sc = planes + cur * 3 * PL;          // y2(zi-2), y3(zi-3), y4(zi-4)
-        T *Sn = planes + (cur ^ 1) * 3 * PL;
-        T d[V];
-        T y2n[V] = {}, y3n[V] = {}, y4n[V] = {}, accn[V] = {};
-        // stage 1 at plane zi-1
-        if (act1) {
-            stage_delta<T, RX, RY>(d, Su, qx, ry, U[0], U[1], un, w1);
+    FusedRegs<T> R;
 #pragma unroll
-            for (int i = 0; i < V; ++i) {
-                y2n[i] = fma(hf, d[i], U[0][i]);
-                accn[i] = c6 * d[i];
-            }
-        }
-        // stage 2 at plane zi-2
-        if (act2) {
-            stage_delta<T, RX, RY>(d, Sc, qx, ry, Y2[0], Y2[1], y2n, w2);
+    for (int i = 0; i < V; ++i) {
 #pragma unroll
-            for (int i = 0; i < V; ++i) {
-                y3n[i] = fma(hf, d[i], U[1][i]);
-                A[0][i] = fma(c3, d[i], A[0][i]);
-            }
-        }
-        // stage 3 at plane zi-3
-        if (act3) {
-            stage_delta<T, RX, RY>(d, Sc + PL, qx, ry, Y3[0], Y3[1], y3n, w2);
+        for (int k = 0; k < 4; ++k) R.U[k][i] = R.A[k][i] = (T)0;
 #pragma unroll
-            for (int i = 0; i < V; ++i) {
-                y4n[i] = U[2][i] + d[i];
-                A[1][i] = fma(c3, d[i], A[1][i]);
-            }
-        }
-        // stage 4 at plane zi-4: the finished step
-        if (act4) {
-            stage_delta<T, RX, RY>(d, Sc + 2 * PL, qx, ry, Y4[0], Y4[1], y4n, w4);
-            const int zo = zi - 4;
-            if (owner && zo >= z_lo) {
-                T o[V];
-#pragma unroll
-                for (int i = 0; i < V; ++i) o[i] = U[3][i] + fma(c6, d[i], A[2][i]);
-                stv<T>(dst + (long long)zo * plane, o);
-            }
-        }
-        stv<T>(Sn + my, y2n);
-        stv<T>(Sn + PL + my, y3n);
-        stv<T>(Sn + 2 * PL + my, y4n);
-        __syncthreads();
-        cur ^= 1;
-#pragma unroll
-        for (int i = 0; i < V; ++i) {
-            U[3][i] = U[2][i]; U[2][i] = U[1][i]; U[1][i] = U[0][i]; U[0][i] = un[i];
-            Y2[1][i] = Y2[0][i]; Y2[0][i] = y2n[i];
-            Y3[1][i] = Y3[0][i]; Y3[0][i] = y3n[i];
-            Y4[1][i] = Y4[0][i]; Y4[0][i] = y4n[i];
-            A[2][i] = A[1][i]; A[1][i] = A[0][i]; A[0][i] = accn[i];
-        }
+        for (int k = 0; k < 3; ++k) R.Y2[k][i] = R.Y3[k][i] = R.Y4[k][i] = (T)0;
+    }
+    for (int base = 0; base < I.n_it; base += 12) {
+        fused_step<T, TX, TY, 0>(I, R, L, base + 0, w1, w2, w4);
+        fused_step<T, TX, TY, 1>(I, R, L, base + 1, w1, w2, w4);
+        fused_step<T, TX, TY, 2>(I, R, L, base + 2, w1, w2, w4);
+        fused_step<T, TX, TY, 3>(I, R, L, base + 3, w1, w2, w4);
+        fused_step<T, TX, TY, 4>(I, R, L, base + 4, w1, w2, w4);
+        fused_step<T, TX, TY, 5>(I, R, L, base + 5, w1, w2, w4);
+        fused_step<T, TX, TY, 6>(I, R, L, base + 6, w1, w2, w4);
+        fused_step<T, TX, TY, 7>(I, R, L, base + 7, w1, w2, w4);
+        fused_step<T, TX, TY, 8>(I, R, L, base + 8, w1, w2, w4);
+        fused_step<T, TX, TY, 9>(I, R, L, base + 9, w1, w2, w4);
+        fused_step<T, TX, TY, 10>(I, R, L, base + 10, w1, w2, w4);
+        fused_step<T, TX, TY, 11>(I, R, L, base + 11, w1, w2, w4);
     }
     cp_async_wait<0>();
 }

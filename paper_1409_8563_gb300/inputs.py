@@ -67,6 +67,22 @@ def batch_instances(seed=0, count=64, sizes=(32, 48, 64, 96, 128), nu0_range=(0.
     return [int(v) for v in ns], [float(v) for v in nu0]
 
 
+def initial_weights(seed=0):
+    """Starting weights of the learned coarse propagator, flattened in the
+    library's order W1[16][2][27] b1 W2[16][16][27] b2 W3 b3 W4[1][16][27] b4:
+    normal with standard deviation sqrt(2 / (27 cin)) for the first three
+    layers (He et al. 2015), zero for the last layer and all biases, so the
+    untrained propagator is the plain shift.  float32."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for li, (ci, co) in enumerate(((2, 16), (16, 16), (16, 16), (16, 1))):
+        W = rng.standard_normal((co, ci, 3, 3, 3)) * np.sqrt(2.0 / (27 * ci))
+        if li == 3:
+            W[:] = 0.0
+        out += [W.ravel(), np.zeros(co)]
+    return np.concatenate(out).astype(np.float32)
+
+
 def random_field(n, seed=0):
     """Standard-normal white noise on the n^3 grid (test inputs)."""
     return np.random.default_rng(seed).standard_normal((n, n, n))

@@ -182,7 +182,7 @@ def test_training_reduces_parareal_iterations():
     pu = torch.empty((16 * N, n, n, n), dtype=torch.float32, device="cuda")
     pf = torch.empty_like(pu)
     sl = ctx.make_pairs(torch.from_numpy(ics).cuda(), pu, pf)
-    ctx.set_coarse_model(to_master(net.init_params(seed=0)))
+    ctx.set_coarse_model(inputs.initial_weights(seed=0))
     hist = ctx.train_coarse(pu, pf, sl, epochs=40, batch=8, lr=2e-3, seed=1)
     assert hist[-1] < 0.5 * hist[0], hist
     u0 = torch.from_numpy(inputs.spectral_ic(n, seed=7, kmax=6)).cuda()
