@@ -269,6 +269,38 @@ parareal_status parareal_profile(parareal_ctx *ctx, int enable);
 parareal_status parareal_profile_read(parareal_ctx *ctx, double *fine_ms, long long *fine_launches,
                                       double *fine_bytes);
 
+/* Defect norms without any device allocation.
+ *
+ * a and b are caller-owned FP64 device arrays of `count` values; out5 is a
+ * caller-owned device array of 5 doubles that receives max|a-b|, max|b|,
+ * sum (a-b)^2, sum b^2 and 1.0 if some a-b is NaN or infinite (else 0.0):
+ * the numbers behind the defect d^k = out5[0] / out5[1].  The paper has no
+ * counterpart of this call.
+ *
+ * It exists for callers that cannot call cudaMalloc: code that records work
+ * into a CUDA graph while stream capture is active (allocation cannot be
+ * captured), code running inside a framework whose caching allocator owns the
+ * device memory (a second allocator would fragment it or break its
+ * accounting), and latency-critical loops that must not wait on the driver's
+ * allocation lock.  The per-block partial sums go to a fixed scratch array
+ * compiled into the library (640 KiB of device memory, held by every GPU that
+ * loads the library until the process exits).
+ *
+ * - count must be at most PARAREAL_NOALLOC_MAX_COUNT; larger counts return
+ *   PARAREAL_E_INVALID and launch nothing (message: parareal_noalloc_last_error).
+ * - Asynchronous on cuda_stream (NULL = default stream): out5 is valid once
+ *   that stream reaches this point.
+ * - The first call on a device looks up the scratch array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ * - All calls share the one scratch array: calls that may overlap on the GPU
+ *   (different streams, concurrent graph replays) race and must be ordered
+ *   by the caller.  Each call overwrites every scratch entry it reads, so no
+ *   clearing is needed between calls. */
+#define PARAREAL_NOALLOC_MAX_COUNT 67108864LL
+parareal_status parareal_diff_norms_noalloc(const double *a, const double *b, long long count,
+                                            double *out5, void *cuda_stream);
+const char *parareal_noalloc_last_error(void);
+
 /* Number of kernel launches this context issued so far (for reporting). */
 long long parareal_launch_count(const parareal_ctx *ctx);
 

@@ -96,6 +96,8 @@ SIGNATURES = {
     "parareal_batch_graph_launches": (ctypes.c_longlong, [_vp]),
     "parareal_batch_last_error": (_cp, [_vp]),
     "parareal_batch_destroy": (None, [_vp]),
+    "parareal_diff_norms_noalloc": (_i, [_vp, _vp, ctypes.c_longlong, _vp, _vp]),
+    "parareal_noalloc_last_error": (_cp, []),
     "parareal_profile": (_i, [_vp, _i]),
     "parareal_profile_read": (_i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]),
     "parareal_launch_count": (ctypes.c_longlong, [_vp]),
