@@ -222,16 +222,20 @@ parareal_status parareal_coarse_model_grad(parareal_ctx *ctx, const float *u, co
 
 /* Autotuner: times every compiled launch shape of the fine step kernel (tile
  * in x and y, z-march chunk, or the per-stage path) on this context's batch
- * of slices, and of the coarse step kernel on the coarse grid, keeps the
- * fastest, and appends it to `cache_path` (JSON lines keyed by grid edge,
+ * of slices and on a single field, and of the coarse step kernel on the
+ * coarse grid, keeps the fastest of each, and appends them to `cache_path`
+ * (JSON lines keyed by grid edge,
  * dtype, batch size and SM count; NULL = no cache).  A cached key is reused
  * without timing.  Uses the iterate as scratch: call before
  * parareal_set_problem.  ms2 (may be NULL): best fine / coarse ms per step
  * (-1 when taken from the cache). */
 parareal_status parareal_autotune(parareal_ctx *ctx, const char *cache_path, double *ms2);
 
-/* The launch shapes in use: {path (0 fused, 1 per-stage), tile_x, tile_y, z chunk}. */
-parareal_status parareal_get_launch_shape(const parareal_ctx *ctx, int *fine4, int *coarse4);
+/* The launch shapes in use, each {path (0 fused, 1 per-stage), tile_x,
+ * tile_y, z chunk}: the batched fine sweep, the coarse steps, and one fine
+ * field at a time (serial fine run, propagate).  Any pointer may be NULL. */
+parareal_status parareal_get_launch_shape(const parareal_ctx *ctx, int *fine4, int *coarse4,
+                                          int *serial4);
 
 /* Batches of independent problems of uneven sizes.  Each instance is a
  * context of its own (its own config, workspace and stream); one round of

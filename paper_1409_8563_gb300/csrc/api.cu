@@ -425,10 +425,13 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
     c->diff_inf.assign(c->N + 1, 0.0);
     c->diff_l2.assign(c->N + 1, 0.0);
     default_tiles(cfg->fine_dtype, c->n, c->N, &c->fine_path, &c->fine_tx, &c->fine_ty, &c->fine_zc);
+    default_tiles(cfg->fine_dtype, c->n, 1, &c->ser_path, &c->ser_tx, &c->ser_ty, &c->ser_zc);
     default_tiles(cfg->fine_dtype, c->nc, 1, &c->coarse_path, &c->coarse_tx, &c->coarse_ty, &c->coarse_zc);
     // explicit launch shapes ("path,tile_x,tile_y,zchunk"), e.g. from the autotuner
     if (!tile_override("PARAREAL_FINE_TILE", cfg->fine_dtype, c->n, &c->fine_path, &c->fine_tx,
                        &c->fine_ty, &c->fine_zc) ||
+        !tile_override("PARAREAL_SERIAL_TILE", cfg->fine_dtype, c->n, &c->ser_path, &c->ser_tx,
+                       &c->ser_ty, &c->ser_zc) ||
         !tile_override("PARAREAL_COARSE_TILE", cfg->fine_dtype, c->nc, &c->coarse_path,
                        &c->coarse_tx, &c->coarse_ty, &c->coarse_zc)) {
         delete c;
@@ -714,8 +717,8 @@ extern "C" parareal_status parareal_serial_fine(parareal_ctx *c, void *dst, int 
         CK(cudaMemcpyAsync(cur, c->U, P * 8, cudaMemcpyDeviceToDevice, c->st));
         double *Fv1 = static_cast<double *>(c->Fv) + P;
         for (int n = 0; n < c->N && s == PARAREAL_OK; ++n) {
-            s = rk4_batch<double>(c, c->n, cur, Fv1, n, 1, c->Nf, c->cfg.dt_fine, c->fine_path,
-                                  c->fine_tx, c->fine_ty, c->fine_zc, static_cast<double *>(c->wA),
+            s = rk4_batch<double>(c, c->n, cur, Fv1, n, 1, c->Nf, c->cfg.dt_fine, c->ser_path,
+                                  c->ser_tx, c->ser_ty, c->ser_zc, static_cast<double *>(c->wA),
                                   static_cast<double *>(c->wB), static_cast<double *>(c->wC));
             if (s == PARAREAL_OK) CK(cudaMemcpyAsync(cur, Fv1, P * 8, cudaMemcpyDeviceToDevice, c->st));
         }
@@ -726,8 +729,8 @@ extern "C" parareal_status parareal_serial_fine(parareal_ctx *c, void *dst, int 
         LK(launch_convert_f64_to_f32(c->U, cur, P, c->st));
         float *Fv1 = static_cast<float *>(c->Fv) + P;
         for (int n = 0; n < c->N && s == PARAREAL_OK; ++n) {
-            s = rk4_batch<float>(c, c->n, cur, Fv1, n, 1, c->Nf, c->cfg.dt_fine, c->fine_path,
-                                 c->fine_tx, c->fine_ty, c->fine_zc, static_cast<float *>(c->wA),
+            s = rk4_batch<float>(c, c->n, cur, Fv1, n, 1, c->Nf, c->cfg.dt_fine, c->ser_path,
+                                 c->ser_tx, c->ser_ty, c->ser_zc, static_cast<float *>(c->wA),
                                  static_cast<float *>(c->wB), static_cast<float *>(c->wC));
             if (s == PARAREAL_OK) CK(cudaMemcpyAsync(cur, Fv1, P * 4, cudaMemcpyDeviceToDevice, c->st));
         }
@@ -786,8 +789,8 @@ static parareal_status propagate_t(parareal_ctx *c, int which, const void *src, 
                 LK(launch_convert_f64_to_f32(in64, reinterpret_cast<float *>(tin), P, c->st));
             else
                 CK(cudaMemcpyAsync(tin, in64, P * 8, cudaMemcpyDeviceToDevice, c->st));
-            s = rk4_batch<T>(c, c->n, tin, tout, first + f, 1, c->Nf, c->cfg.dt_fine, c->fine_path,
-                             c->fine_tx, c->fine_ty, c->fine_zc, static_cast<T *>(c->wA),
+            s = rk4_batch<T>(c, c->n, tin, tout, first + f, 1, c->Nf, c->cfg.dt_fine, c->ser_path,
+                             c->ser_tx, c->ser_ty, c->ser_zc, static_cast<T *>(c->wA),
                              static_cast<T *>(c->wB), static_cast<T *>(c->wC));
             if (s != PARAREAL_OK) return s;
             if (std::is_same<T, float>::value)
@@ -865,7 +868,7 @@ static parareal_status time_shape(parareal_ctx *c, int m, int count, int path, i
 // chunked z marches, and the per-stage path.
 static void candidates(int dtype, int m, std::vector<std::array<int, 4>> *out)
 {
-    const int shapes[][2] = {{64, 16}, {64, 8}, {32, 16}, {32, 8}, {16, 16}, {16, 8}};
+    const int shapes[][2] = {{64, 32}, {64, 16}, {64, 8}, {32, 16}, {32, 8}, {16, 16}, {16, 8}};
     for (auto &sh : shapes) {
         if (!rk4_fused_supported(dtype, m, sh[0], sh[1])) continue;
         for (int zc = m; zc >= 8; zc /= 2) {
@@ -959,6 +962,19 @@ extern "C" parareal_status parareal_autotune(parareal_ctx *c, const char *cache_
         s = tune_one<float>(c, cache_path, c->n, c->N, c->cfg.dt_fine, &c->fine_path, &c->fine_tx,
                             &c->fine_ty, &c->fine_zc, &fms);
     if (s != PARAREAL_OK) return s;
+    if (c->N > 1) {
+        // one fine field at a time (serial fine run, propagate)
+        double sms = 0.0;
+        if (c->f64)
+            s = tune_one<double>(c, cache_path, c->n, 1, c->cfg.dt_fine, &c->ser_path, &c->ser_tx,
+                                 &c->ser_ty, &c->ser_zc, &sms);
+        else
+            s = tune_one<float>(c, cache_path, c->n, 1, c->cfg.dt_fine, &c->ser_path, &c->ser_tx,
+                                &c->ser_ty, &c->ser_zc, &sms);
+        if (s != PARAREAL_OK) return s;
+    } else {
+        c->ser_path = c->fine_path; c->ser_tx = c->fine_tx; c->ser_ty = c->fine_ty; c->ser_zc = c->fine_zc;
+    }
     if (c->cfg.coarse_kind == PARAREAL_COARSE_STENCIL && c->nc >= 8) {
         // the coarse sweep runs one field at a time on the coarse grid
         void *saveC = c->wC;
@@ -978,10 +994,12 @@ extern "C" parareal_status parareal_autotune(parareal_ctx *c, const char *cache_
     return PARAREAL_OK;
 }
 
-extern "C" parareal_status parareal_get_launch_shape(const parareal_ctx *c, int *fine4, int *coarse4)
+extern "C" parareal_status parareal_get_launch_shape(const parareal_ctx *c, int *fine4, int *coarse4,
+                                                     int *serial4)
 {
     if (!c) return PARAREAL_E_INVALID;
     if (fine4) { fine4[0] = c->fine_path; fine4[1] = c->fine_tx; fine4[2] = c->fine_ty; fine4[3] = c->fine_zc; }
+    if (serial4) { serial4[0] = c->ser_path; serial4[1] = c->ser_tx; serial4[2] = c->ser_ty; serial4[3] = c->ser_zc; }
     if (coarse4) { coarse4[0] = c->coarse_path; coarse4[1] = c->coarse_tx; coarse4[2] = c->coarse_ty; coarse4[3] = c->coarse_zc; }
     return PARAREAL_OK;
 }

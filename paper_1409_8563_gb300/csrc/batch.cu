@@ -232,6 +232,8 @@ extern "C" parareal_status parareal_batch_autotune(parareal_batch *b, const char
         }
         c->fine_path = same->fine_path; c->fine_tx = same->fine_tx;
         c->fine_ty = same->fine_ty; c->fine_zc = same->fine_zc;
+        c->ser_path = same->ser_path; c->ser_tx = same->ser_tx;
+        c->ser_ty = same->ser_ty; c->ser_zc = same->ser_zc;
         c->coarse_path = same->coarse_path; c->coarse_tx = same->coarse_tx;
         c->coarse_ty = same->coarse_ty; c->coarse_zc = same->coarse_zc;
         c->has_problem = false;

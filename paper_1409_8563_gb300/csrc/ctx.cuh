@@ -62,7 +62,10 @@ struct parareal_ctx {
     int k_total = 0;
     std::vector<double> diff_inf, diff_l2;   // last iteration, per slice
 
+    // launch shapes: the batched fine sweep (N fields), one fine field (serial
+    // fine run, propagate) and one coarse field
     int fine_path = PATH_FUSED, fine_tx = 64, fine_ty = 16, fine_zc = 0;
+    int ser_path = PATH_FUSED, ser_tx = 64, ser_ty = 16, ser_zc = 0;
     int coarse_path = PATH_FUSED, coarse_tx = 32, coarse_ty = 8, coarse_zc = 0;
 
     NetState net;

@@ -97,6 +97,10 @@ struct FusedShape {
     static constexpr int RING = 6;             // u planes resident (divides the unroll of 12)
     // u ring [RING][PL], stage planes [2][3][PL], u edges [RING][2][EL], stage edges [2][3][2][EL]
     static constexpr size_t SMEM = ((size_t)(RING + 6) * PL + (size_t)(2 * RING + 12) * EL) * sizeof(T);
+    // CTAs per SM the register allocation is held to: as many as 64K
+    // registers allow at >= 128 registers per thread (latency hiding comes
+    // from independent CTAs: every CTA waits at a barrier once per plane)
+    static constexpr int MINB = NT * 2 * 128 <= 65536 ? 2 : 1;
 };
 
 // 16-byte asynchronous global->shared copy (L2 only, bypassing L1) and its
@@ -148,6 +152,88 @@ __device__ __forceinline__ void stage_delta(T (&d)[VecT<T>::V], const T *__restr
         acc = fma(w[6], zp[i], acc);
         d[i] = acc;
     }
+}
+
+// FP32: the same arithmetic on pairs of points with the packed FP32x2
+// instructions (two independent FP32 operations, each rounded as its scalar
+// counterpart, per issued instruction): identical results, half the issue
+// slots for the stencil's multiply-adds.
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+
+template <>
+__device__ __forceinline__ void stage_delta<float>(float (&d)[4], const float *__restrict__ Sp,
+                                                   const float *__restrict__ E, int EL,
+                                                   const FusedLane &L, const float (&c)[4],
+                                                   const float (&zm)[4], const float (&zp)[4],
+                                                   const float (&w)[7])
+{
+    float ym[4], yp[4];
+    ldv<float>(Sp + L.ym, ym);
+    ldv<float>(Sp + L.yp, yp);
+    const float left = E[EL + L.el];
+    const float right = E[L.er];
+    float2 lo = __fmul2_rn(bc(w[0]), pk(c[0], c[1]));
+    float2 hi = __fmul2_rn(bc(w[0]), pk(c[2], c[3]));
+    lo = __ffma2_rn(bc(w[1]), pk(left, c[0]), lo);
+    hi = __ffma2_rn(bc(w[1]), pk(c[1], c[2]), hi);
+    lo = __ffma2_rn(bc(w[2]), pk(c[1], c[2]), lo);
+    hi = __ffma2_rn(bc(w[2]), pk(c[3], right), hi);
+    lo = __ffma2_rn(bc(w[3]), pk(ym[0], ym[1]), lo);
+    hi = __ffma2_rn(bc(w[3]), pk(ym[2], ym[3]), hi);
+    lo = __ffma2_rn(bc(w[4]), pk(yp[0], yp[1]), lo);
+    hi = __ffma2_rn(bc(w[4]), pk(yp[2], yp[3]), hi);
+    lo = __ffma2_rn(bc(w[5]), pk(zm[0], zm[1]), lo);
+    hi = __ffma2_rn(bc(w[5]), pk(zm[2], zm[3]), hi);
+    lo = __ffma2_rn(bc(w[6]), pk(zp[0], zp[1]), lo);
+    hi = __ffma2_rn(bc(w[6]), pk(zp[2], zp[3]), hi);
+    d[0] = lo.x; d[1] = lo.y; d[2] = hi.x; d[3] = hi.y;
+}
+
+// z[i] = fma(a, x[i], y[i]) over a vector (packed for FP32).
+template <typename T>
+__device__ __forceinline__ void vfma(T (&z)[VecT<T>::V], T a, const T (&x)[VecT<T>::V],
+                                     const T (&y)[VecT<T>::V])
+{
+#pragma unroll
+    for (int i = 0; i < VecT<T>::V; ++i) z[i] = fma(a, x[i], y[i]);
+}
+template <>
+__device__ __forceinline__ void vfma<float>(float (&z)[4], float a, const float (&x)[4],
+                                            const float (&y)[4])
+{
+    const float2 lo = __ffma2_rn(bc(a), pk(x[0], x[1]), pk(y[0], y[1]));
+    const float2 hi = __ffma2_rn(bc(a), pk(x[2], x[3]), pk(y[2], y[3]));
+    z[0] = lo.x; z[1] = lo.y; z[2] = hi.x; z[3] = hi.y;
+}
+// z[i] = x[i] + y[i]
+template <typename T>
+__device__ __forceinline__ void vadd(T (&z)[VecT<T>::V], const T (&x)[VecT<T>::V],
+                                     const T (&y)[VecT<T>::V])
+{
+#pragma unroll
+    for (int i = 0; i < VecT<T>::V; ++i) z[i] = x[i] + y[i];
+}
+template <>
+__device__ __forceinline__ void vadd<float>(float (&z)[4], const float (&x)[4], const float (&y)[4])
+{
+    const float2 lo = __fadd2_rn(pk(x[0], x[1]), pk(y[0], y[1]));
+    const float2 hi = __fadd2_rn(pk(x[2], x[3]), pk(y[2], y[3]));
+    z[0] = lo.x; z[1] = lo.y; z[2] = hi.x; z[3] = hi.y;
+}
+// z[i] = a * x[i]
+template <typename T>
+__device__ __forceinline__ void vmul(T (&z)[VecT<T>::V], T a, const T (&x)[VecT<T>::V])
+{
+#pragma unroll
+    for (int i = 0; i < VecT<T>::V; ++i) z[i] = a * x[i];
+}
+template <>
+__device__ __forceinline__ void vmul<float>(float (&z)[4], float a, const float (&x)[4])
+{
+    const float2 lo = __fmul2_rn(bc(a), pk(x[0], x[1]));
+    const float2 hi = __fmul2_rn(bc(a), pk(x[2], x[3]));
+    z[0] = lo.x; z[1] = lo.y; z[2] = hi.x; z[3] = hi.y;
 }
 
 // Register windows of one thread, indexed by iteration modulo their period:
@@ -207,37 +293,28 @@ __device__ __forceinline__ void fused_step(FusedIter<T> &I, FusedRegs<T> &R, con
     // stage 1 at the plane of iteration it-1
     if (I.act1) {
         stage_delta<T>(d, Su, Eu, EL, L, R.U[(PH + 3) % 4], R.U[(PH + 2) % 4], un, w1);
-#pragma unroll
-        for (int i = 0; i < V; ++i) {
-            y2n[i] = fma(hf, d[i], R.U[(PH + 3) % 4][i]);
-            accn[i] = c6 * d[i];
-        }
+        vfma<T>(y2n, hf, d, R.U[(PH + 3) % 4]);
+        vmul<T>(accn, c6, d);
     }
     // stage 2 at the plane of iteration it-2
     if (I.act2) {
         stage_delta<T>(d, Sc, Ec, EL, L, R.Y2[(PH + 2) % 3], R.Y2[(PH + 1) % 3], y2n, w2);
-#pragma unroll
-        for (int i = 0; i < V; ++i) {
-            y3n[i] = fma(hf, d[i], R.U[(PH + 2) % 4][i]);
-            R.A[(PH + 3) % 4][i] = fma(c3, d[i], R.A[(PH + 3) % 4][i]);
-        }
+        vfma<T>(y3n, hf, d, R.U[(PH + 2) % 4]);
+        vfma<T>(R.A[(PH + 3) % 4], c3, d, R.A[(PH + 3) % 4]);
     }
     // stage 3 at the plane of iteration it-3
     if (I.act3) {
         stage_delta<T>(d, Sc + PL, Ec + 2 * EL, EL, L, R.Y3[(PH + 2) % 3], R.Y3[(PH + 1) % 3], y3n, w2);
-#pragma unroll
-        for (int i = 0; i < V; ++i) {
-            y4n[i] = R.U[(PH + 1) % 4][i] + d[i];
-            R.A[(PH + 2) % 4][i] = fma(c3, d[i], R.A[(PH + 2) % 4][i]);
-        }
+        vadd<T>(y4n, R.U[(PH + 1) % 4], d);
+        vfma<T>(R.A[(PH + 2) % 4], c3, d, R.A[(PH + 2) % 4]);
     }
     // stage 4 at the plane of iteration it-4: the finished step
     if (I.act4) {
         stage_delta<T>(d, Sc + 2 * PL, Ec + 4 * EL, EL, L, R.Y4[(PH + 2) % 3], R.Y4[(PH + 1) % 3], y4n, w4);
         if (I.owner && it >= 8) {
-            T o[V];
-#pragma unroll
-            for (int i = 0; i < V; ++i) o[i] = R.U[PH % 4][i] + fma(c6, d[i], R.A[(PH + 1) % 4][i]);
+            T o[V], inc[V];
+            vfma<T>(inc, c6, d, R.A[(PH + 1) % 4]);
+            vadd<T>(o, R.U[PH % 4], inc);
             stv<T>(I.dst + I.ooff, o);
         }
     }
@@ -269,7 +346,7 @@ __device__ __forceinline__ void fused_step(FusedIter<T> &I, FusedRegs<T> &R, con
 // z_lo - 4 + it - s).  The z loop is unrolled by 12, a multiple of every
 // register window's period, so the windows never move between registers.
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(FusedShape<T, TX, TY>::NT, 1)
+__global__ void __launch_bounds__(FusedShape<T, TX, TY>::NT, FusedShape<T, TX, TY>::MINB)
 rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int tiles_x,
                  int tiles_y, int zchunk, int nzc)
 {
@@ -284,8 +361,14 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
     __shared__ T s_w[3][7];                        // stage 1, stages 2-3, stage 4
 
     const int tid = threadIdx.x;
+    // Rows in order of the stages they need: the TY inner rows (all four)
+    // first, then the halo rows 3, RY-4 (three stages), 2, RY-3, 1, RY-2 and
+    // 0, RY-1 (none), so the halo rows share warps and those warps skip
+    // whole stages.
     const int qx = tid % QX;
-    const int ry = tid / QX;
+    const int ri = tid / QX;
+    const int hj = ri - TY;
+    const int ry = ri < TY ? 4 + ri : ((hj & 1) ? RY - 4 + (hj >> 1) : 3 - (hj >> 1));
     int b = blockIdx.x;
     const int zc = b % nzc; b /= nzc;
     const int tx = b % tiles_x; b /= tiles_x;
@@ -403,6 +486,7 @@ static cudaError_t configure_shape()
 
 // Tile shapes compiled for the fused kernel.
 #define PR_FUSED_SHAPES(X) \
+    X(float, 64, 32)       \
     X(float, 64, 16)       \
     X(float, 64, 8)        \
     X(float, 32, 16)       \

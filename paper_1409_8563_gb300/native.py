@@ -86,7 +86,7 @@ SIGNATURES = {
     "parareal_train_coarse": (_i, [_vp, _vp, _vp, _ip, _i, _vp, _dp]),
     "parareal_coarse_model_grad": (_i, [_vp, _vp, _vp, _ip, _i, _vp, _dp]),
     "parareal_autotune": (_i, [_vp, _cp, _dp]),
-    "parareal_get_launch_shape": (_i, [_vp, _ip, _ip]),
+    "parareal_get_launch_shape": (_i, [_vp, _ip, _ip, _ip]),
     "parareal_batch_create": (_i, [ctypes.POINTER(Config), _i, _vp, ctypes.POINTER(_vp)]),
     "parareal_batch_set_problem": (_i, [_vp, _i, _vp, _i, _i]),
     "parareal_batch_serial_fine": (_i, [_vp, _i]),
@@ -271,9 +271,10 @@ class Parareal:
         return ms[0], ms[1]
 
     def launch_shape(self):
-        f, c = (ctypes.c_int * 4)(), (ctypes.c_int * 4)()
-        self._check(lib().parareal_get_launch_shape(self._h, f, c))
-        return tuple(f[:]), tuple(c[:])
+        """(batched fine sweep, coarse steps, single fine field) launch shapes."""
+        f, c, s = (ctypes.c_int * 4)(), (ctypes.c_int * 4)(), (ctypes.c_int * 4)()
+        self._check(lib().parareal_get_launch_shape(self._h, f, c, s))
+        return tuple(f[:]), tuple(c[:]), tuple(s[:])
 
     def profile(self, enable=True):
         return self._check(lib().parareal_profile(self._h, int(enable)))

@@ -17,14 +17,17 @@ pytestmark = pytest.mark.gpu
 
 
 def small_batch():
-    # uneven sizes and viscosities, N = 4 slices, coarse grid n/4 where it is >= 4
+    # uneven sizes and viscosities, N = 4 slices, T = 1/16, dt_F = 2^-m from the
+    # batch rule, coarse step 4 dt_F on n / r
     specs = [(16, 0.004, 2), (24, 0.01, 2), (32, 0.02, 4), (48, 0.006, 4), (16, 0.015, 1)]
     cfgs, u0s = [], []
     for k, (n, nu0, r) in enumerate(specs):
-        cfg, u0 = configs.small(n=n, n_slices=4, dtype=native.F32, r=r, nf=8, nc=2, seed=k)
-        cfg.nu0 = nu0
+        m = configs.batch_dt_exponent(n, nu0)
+        cfg = native.Config.make(n, 4, 1.0 / 16, 2.0 ** -m, 4 * 2.0 ** -m, r,
+                                 fine_dtype=native.F32, nu0=nu0)
+        assert native.stability(cfg)[0] == native.OK
         cfgs.append(cfg)
-        u0s.append(u0)
+        u0s.append(inputs.spectral_ic(n, seed=k, kmax=max(2, n // 8)))
     return cfgs, u0s
 
 
@@ -71,7 +74,7 @@ def test_autotune_picks_a_valid_shape_and_caches_it(tmp_path):
     ctx = native.Parareal(cfg)
     fms, cms = ctx.autotune(cache)
     assert fms > 0
-    fine, coarse = ctx.launch_shape()
+    fine, coarse, serial = ctx.launch_shape()
     lines = [json.loads(l) for l in open(cache)]
     assert any(l["shape"] == list(fine) for l in lines)
     # results with the tuned shape still match the oracle
