@@ -103,7 +103,15 @@ typedef struct {
     int nu_mode;           /* PARAREAL_NU_STAGE or PARAREAL_NU_FROZEN */
     int coarse_kind;       /* PARAREAL_COARSE_* */
     int allow_unstable;    /* nonzero: stability pre-check failures become a warning */
+    int learned_skip;      /* PARAREAL_SKIP_*: the skip path of the learned propagator */
 } parareal_config;
+
+/* Skip path of the learned coarse propagator (coarse_kind LEARNED / SHIFT):
+ * SHIFT   G = S(u) + Net([S(u), nu/nu0]) on the grid n / coarse_factor;
+ * STENCIL G = Gs(u) + Net([Gs(u), nu/nu0]) on the fine grid, Gs the stencil
+ *         coarse propagator (RK4 on n / coarse_factor at dt_coarse, box
+ *         restriction, trilinear prolongation): the net learns F - Gs. */
+enum { PARAREAL_SKIP_SHIFT = 0, PARAREAL_SKIP_STENCIL = 1 };
 
 /* Validate cfg, run the stability pre-check, allocate all device workspace
  * and return a context bound to `cuda_stream` (a cudaStream_t; NULL = default
@@ -201,7 +209,9 @@ parareal_status parareal_get_coarse_model(parareal_ctx *ctx, float *w, int mem);
  * (device, n^3 each); for each the serial fine trajectory over all slices
  * gives pairs (u_n, F(u_n)), n = 0..N_p-1, written at pair index ic*N_p + n
  * of pairs_u / pairs_f (device, FP32, on the net's grid: (n/coarse_factor)^3
- * each).  pair_slice (host, may be NULL) receives n for every pair. */
+ * each with the SHIFT skip, n^3 with the STENCIL skip).  With the STENCIL skip
+ * pairs_u holds the net's input Gs(u_n) instead of u_n.  pair_slice (host,
+ * may be NULL) receives n for every pair. */
 parareal_status parareal_make_pairs(parareal_ctx *ctx, const float *ics, int n_ics, float *pairs_u,
                                     float *pairs_f, int *pair_slice);
 

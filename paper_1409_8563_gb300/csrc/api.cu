@@ -92,6 +92,7 @@ static parareal_status validate(const parareal_config *cfg, long long *Nf, long 
     if (cfg->fine_dtype != PARAREAL_F32 && cfg->fine_dtype != PARAREAL_F64) { *msg = "fine_dtype"; return PARAREAL_E_INVALID; }
     if (cfg->nu_mode != PARAREAL_NU_STAGE && cfg->nu_mode != PARAREAL_NU_FROZEN) { *msg = "nu_mode"; return PARAREAL_E_INVALID; }
     if (cfg->coarse_kind < PARAREAL_COARSE_STENCIL || cfg->coarse_kind > PARAREAL_COARSE_SHIFT) { *msg = "coarse_kind"; return PARAREAL_E_INVALID; }
+    if (cfg->learned_skip != PARAREAL_SKIP_SHIFT && cfg->learned_skip != PARAREAL_SKIP_STENCIL) { *msg = "learned_skip"; return PARAREAL_E_INVALID; }
     const double slice = cfg->T / cfg->n_slices;
     if (!is_integer_ratio(slice, cfg->dt_fine, Nf)) { *msg = "T/(n_slices dt_fine) must be an integer"; return PARAREAL_E_INVALID; }
     if (!is_integer_ratio(slice, cfg->dt_coarse, Nc)) { *msg = "T/(n_slices dt_coarse) must be an integer"; return PARAREAL_E_INVALID; }
@@ -108,7 +109,8 @@ extern "C" parareal_status parareal_stability(const parareal_config *cfg, double
     const double lo = cfg->nu0 * (1.0 - std::fabs(cfg->nu_amp));
     const double hi = cfg->nu0 * (1.0 + std::fabs(cfg->nu_amp));
     const double gf = rk4_growth(cfg->n, cfg->dt_fine, cfg->a, lo, hi);
-    const double gc = cfg->coarse_kind == PARAREAL_COARSE_STENCIL
+    const double gc = (cfg->coarse_kind == PARAREAL_COARSE_STENCIL ||
+                       cfg->learned_skip == PARAREAL_SKIP_STENCIL)
                           ? rk4_growth(cfg->n / cfg->coarse_factor, cfg->dt_coarse, cfg->a, lo, hi)
                           : 0.0;
     if (growth2) { growth2[0] = gf; growth2[1] = gc; }
@@ -247,13 +249,58 @@ static parareal_status fine_sweep_t(parareal_ctx *c, int first, int count)
                         c->fine_tx, c->fine_ty, c->fine_zc, ws1, ws2, ws3);
 }
 
-// G(U_in) for slice s into `out` (Pc T fields when r > 1, P doubles when r = 1).
+// The stencil coarse propagator of slice s on the fine grid, in FP64: RK4 on
+// the grid coarsened by r (box restriction before, trilinear prolongation
+// after) or on the fine grid itself when r = 1.
+template <typename T>
+static parareal_status stencil_g_fine_t(parareal_ctx *c, const double *u, int s, double *out)
+{
+    T *cA = static_cast<T *>(c->cA), *cB = static_cast<T *>(c->cB), *cC = static_cast<T *>(c->cC),
+      *cD = static_cast<T *>(c->cD);
+    parareal_status ps;
+    if (c->r > 1) {
+        LK(launch_restrict<T>(u, c->n, c->r, cA, c->st));
+        ps = rk4_batch<T>(c, c->nc, cA, cB, s, 1, c->Nc, c->cfg.dt_coarse, c->coarse_path,
+                          c->coarse_tx, c->coarse_ty, c->coarse_zc, cC, cD, cA);
+        if (ps != PARAREAL_OK) return ps;
+        // prolongation of the coarse result (the correction kernel with no
+        // fine value and no old coarse value writes exactly that)
+        LK((launch_correct<T, T>(nullptr, cB, nullptr, out, c->n, c->r, c->partials, c->nblk, c->st)));
+        return PARAREAL_OK;
+    }
+    if (std::is_same<T, float>::value) {
+        LK(launch_convert_f64_to_f32(u, reinterpret_cast<float *>(cA), c->P, c->st));
+        ps = rk4_batch<T>(c, c->n, cA, cB, s, 1, c->Nc, c->cfg.dt_coarse, c->coarse_path,
+                          c->coarse_tx, c->coarse_ty, c->coarse_zc, cC, cD, cA);
+        if (ps != PARAREAL_OK) return ps;
+        LK(launch_convert_f32_to_f64(reinterpret_cast<const float *>(cB), out, c->P, c->st));
+        return PARAREAL_OK;
+    }
+    return rk4_batch<T>(c, c->n, reinterpret_cast<const T *>(u), reinterpret_cast<T *>(out), s, 1,
+                        c->Nc, c->cfg.dt_coarse, c->coarse_path, c->coarse_tx, c->coarse_ty,
+                        c->coarse_zc, cB, cC, cD);
+}
+
+parareal_status stencil_g_fine(parareal_ctx *c, const double *u, int s, double *out)
+{
+    return c->f64 ? stencil_g_fine_t<double>(c, u, s, out) : stencil_g_fine_t<float>(c, u, s, out);
+}
+
+// G(U_in) for slice s into `out` (Pc T fields when G's output is coarse,
+// else P doubles).
 template <typename T>
 static parareal_status coarse_apply_t(parareal_ctx *c, const double *Uin, int s, void *out)
 {
     T *cA = static_cast<T *>(c->cA), *cB = static_cast<T *>(c->cB), *cC = static_cast<T *>(c->cC),
       *cD = static_cast<T *>(c->cD);
     if (c->cfg.coarse_kind != PARAREAL_COARSE_STENCIL) {
+        if (c->cfg.learned_skip == PARAREAL_SKIP_STENCIL) {
+            // the net corrects the stencil propagator's output on the fine grid
+            double *gs = c->tmpd + c->P;
+            parareal_status ps = stencil_g_fine(c, Uin, s, gs);
+            if (ps != PARAREAL_OK) return ps;
+            return net_apply<double, double>(c, gs, s, static_cast<double *>(out));
+        }
         // shift + convolution net, on the fine grid or on the restricted grid
         if (c->r == 1) return net_apply<double, double>(c, Uin, s, static_cast<double *>(out));
         LK(launch_restrict<T>(Uin, c->n, c->r, cA, c->st));
@@ -286,7 +333,7 @@ static parareal_status correct_t(parareal_ctx *c, int s, const void *gnew, const
 {
     const T *Fv = with_fine ? static_cast<const T *>(c->Fv) + (long long)(s + 1) * c->P : nullptr;
     double *U = c->U + (long long)(s + 1) * c->P;
-    if (c->r > 1) {
+    if (!c->g_fine) {
         LK((launch_correct<T, T>(Fv, static_cast<const T *>(gnew), static_cast<const T *>(gold), U,
                                  c->n, c->r, c->partials, c->nblk, c->st)));
     } else {
@@ -444,7 +491,11 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
     };
     const size_t e = c->esz;
     const size_t P = (size_t)c->P, Pc = (size_t)c->Pc, N = (size_t)c->N;
-    const size_t gbytes = c->r > 1 ? Pc * e : P * sizeof(double);
+    // G's output: a coarse T field when G ends on the coarse grid (stencil G,
+    // or a net on the restricted grid), else a fine FP64 field
+    c->g_fine = c->r == 1 || (cfg->coarse_kind != PARAREAL_COARSE_STENCIL &&
+                              cfg->learned_skip == PARAREAL_SKIP_STENCIL);
+    const size_t gbytes = c->g_fine ? P * sizeof(double) : Pc * e;
     bool ok = cudaGetDevice(&c->dev) == cudaSuccess;
     ok = ok && alloc((void **)&c->U, (N + 1) * P * sizeof(double));
     ok = ok && alloc(&c->Fv, (N + 1) * P * e);
@@ -804,7 +855,7 @@ static parareal_status propagate_t(parareal_ctx *c, int which, const void *src, 
             // null F and null old value, written into res64
             CK(cudaMemsetAsync(res64, 0, P * 8, c->st));
             const T *nullT = nullptr;
-            if (c->r > 1) {
+            if (!c->g_fine) {
                 LK((launch_correct<T, T>(nullT, static_cast<const T *>(c->gspare), nullptr, res64,
                                          c->n, c->r, c->partials, c->nblk, c->st)));
             } else {
@@ -975,7 +1026,8 @@ extern "C" parareal_status parareal_autotune(parareal_ctx *c, const char *cache_
     } else {
         c->ser_path = c->fine_path; c->ser_tx = c->fine_tx; c->ser_ty = c->fine_ty; c->ser_zc = c->fine_zc;
     }
-    if (c->cfg.coarse_kind == PARAREAL_COARSE_STENCIL && c->nc >= 8) {
+    if ((c->cfg.coarse_kind == PARAREAL_COARSE_STENCIL ||
+         c->cfg.learned_skip == PARAREAL_SKIP_STENCIL) && c->nc >= 8) {
         // the coarse sweep runs one field at a time on the coarse grid
         void *saveC = c->wC;
         c->wC = c->cA;   // input of the timed coarse steps

@@ -43,6 +43,7 @@ struct parareal_ctx {
     long long P = 0, Pc = 0, Nf = 0, Nc = 0;
     bool f64 = false;
     size_t esz = 4;
+    bool g_fine = true;           // G's output is a fine FP64 field (else coarse T)
 
     double *U = nullptr;
     void *Fv = nullptr;
@@ -104,6 +105,10 @@ parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, int first
 // api.cu: one Parareal iteration split into device work and host bookkeeping
 parareal_status iter_enqueue(parareal_ctx *c);
 parareal_status iter_finish(parareal_ctx *c, double *dmax, double *l2max, double *d);
+
+// api.cu: the stencil coarse propagator of slice s, prolonged to the fine
+// grid in FP64 (the skip path of the stencil-corrected learned propagator)
+parareal_status stencil_g_fine(parareal_ctx *c, const double *u, int s, double *out);
 
 // learned.cu
 parareal_status net_setup(parareal_ctx *c);

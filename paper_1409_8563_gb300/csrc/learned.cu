@@ -38,12 +38,16 @@ static bool dalloc(void **p, size_t bytes)
 parareal_status net_setup(parareal_ctx *c)
 {
     NetState &S = c->net;
-    S.m = c->n / c->r;
-    if (S.m % 8) return fail(c, PARAREAL_E_INVALID, "the learned propagator needs a grid edge n/coarse_factor that is a multiple of 8");
+    // SHIFT skip: the net runs on the grid n/r after the shift S; STENCIL
+    // skip: the net corrects the stencil propagator's prolonged output on the
+    // fine grid (no shift: the stencil propagator already transports)
+    const bool stencil_skip = c->cfg.learned_skip == PARAREAL_SKIP_STENCIL;
+    S.m = stencil_skip ? c->n : c->n / c->r;
+    if (S.m % 8) return fail(c, PARAREAL_E_INVALID, "the learned propagator needs a grid edge that is a multiple of 8");
     S.Pm = (long long)S.m * S.m * S.m;
     const double slice = c->cfg.T / c->N;
     for (int d = 0; d < 3; ++d) {
-        const long long k = std::llround(c->cfg.a[d] * slice * S.m);
+        const long long k = stencil_skip ? 0 : std::llround(c->cfg.a[d] * slice * S.m);
         S.shift[d] = (int)(((k % S.m) + S.m) % S.m);
     }
     CK(configure_net_kernels());
@@ -319,9 +323,11 @@ static parareal_status make_pairs_t(parareal_ctx *c, const float *ics, int n_ics
     const size_t fb = (size_t)n_ics * P * sizeof(T);
     T *st = nullptr, *w1 = nullptr, *w2 = nullptr, *w3 = nullptr, *nx = nullptr;
     double *tmp = nullptr;
+    const bool restrict_pairs = c->net.m != c->n;          // net on the restricted grid
+    const bool stencil_skip = c->cfg.learned_skip == PARAREAL_SKIP_STENCIL;
     bool ok = dalloc((void **)&st, fb) && dalloc((void **)&w1, fb) && dalloc((void **)&w2, fb) &&
               dalloc((void **)&w3, fb) && dalloc((void **)&nx, fb) &&
-              (c->r == 1 || dalloc((void **)&tmp, (size_t)P * 8));
+              (!(restrict_pairs || stencil_skip) || dalloc((void **)&tmp, (size_t)P * 8));
     auto cleanup = [&]() {
         for (void *q : {(void *)st, (void *)w1, (void *)w2, (void *)w3, (void *)nx, (void *)tmp})
             if (q) cudaFree(q);
@@ -333,7 +339,7 @@ static parareal_status make_pairs_t(parareal_ctx *c, const float *ics, int n_ics
     const long long Pm = c->net.Pm;
     auto emit = [&](const T *field, float *dst) -> parareal_status {
         // one field on the fine grid -> the net's grid, FP32
-        if (c->r == 1) {
+        if (!restrict_pairs) {
             if (std::is_same<T, float>::value)
                 CK(cudaMemcpyAsync(dst, field, P * 4, cudaMemcpyDeviceToDevice, c->st));
             else
@@ -352,9 +358,22 @@ static parareal_status make_pairs_t(parareal_ctx *c, const float *ics, int n_ics
         CK(cudaMemcpyAsync(st, ics, fb, cudaMemcpyDeviceToDevice, c->st));
     else
         LK(launch_convert_f32_to_f64(ics, reinterpret_cast<double *>(st), (long long)n_ics * P, c->st));
+    // STENCIL skip: the net's input is the stencil propagator's output Gs(u_n)
+    auto emit_skip = [&](const T *field, int slice, float *dst) -> parareal_status {
+        if (std::is_same<T, float>::value)
+            LK(launch_convert_f32_to_f64(reinterpret_cast<const float *>(field), tmp, P, c->st));
+        else
+            CK(cudaMemcpyAsync(tmp, field, P * 8, cudaMemcpyDeviceToDevice, c->st));
+        double *gs = c->tmpd + P;
+        parareal_status ps = stencil_g_fine(c, tmp, slice, gs);
+        if (ps != PARAREAL_OK) return ps;
+        LK(launch_convert_f64_to_f32(gs, dst, P, c->st));
+        return PARAREAL_OK;
+    };
     for (int n = 0; n < c->N && s == PARAREAL_OK; ++n) {
         for (int i = 0; i < n_ics && s == PARAREAL_OK; ++i) {
-            s = emit(st + (size_t)i * P, pu + ((size_t)i * c->N + n) * Pm);
+            float *dst = pu + ((size_t)i * c->N + n) * Pm;
+            s = stencil_skip ? emit_skip(st + (size_t)i * P, n, dst) : emit(st + (size_t)i * P, dst);
             if (pair_slice) pair_slice[i * c->N + n] = n;
         }
         if (s != PARAREAL_OK) break;

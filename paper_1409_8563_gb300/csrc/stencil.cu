@@ -154,57 +154,13 @@ __device__ __forceinline__ void stage_delta(T (&d)[VecT<T>::V], const T *__restr
     }
 }
 
-// FP32: the same arithmetic on pairs of points with the packed FP32x2
-// instructions (two independent FP32 operations, each rounded as its scalar
-// counterpart, per issued instruction): identical results, half the issue
-// slots for the stencil's multiply-adds.
-__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
-
-template <>
-__device__ __forceinline__ void stage_delta<float>(float (&d)[4], const float *__restrict__ Sp,
-                                                   const float *__restrict__ E, int EL,
-                                                   const FusedLane &L, const float (&c)[4],
-                                                   const float (&zm)[4], const float (&zp)[4],
-                                                   const float (&w)[7])
-{
-    float ym[4], yp[4];
-    ldv<float>(Sp + L.ym, ym);
-    ldv<float>(Sp + L.yp, yp);
-    const float left = E[EL + L.el];
-    const float right = E[L.er];
-    float2 lo = __fmul2_rn(bc(w[0]), pk(c[0], c[1]));
-    float2 hi = __fmul2_rn(bc(w[0]), pk(c[2], c[3]));
-    lo = __ffma2_rn(bc(w[1]), pk(left, c[0]), lo);
-    hi = __ffma2_rn(bc(w[1]), pk(c[1], c[2]), hi);
-    lo = __ffma2_rn(bc(w[2]), pk(c[1], c[2]), lo);
-    hi = __ffma2_rn(bc(w[2]), pk(c[3], right), hi);
-    lo = __ffma2_rn(bc(w[3]), pk(ym[0], ym[1]), lo);
-    hi = __ffma2_rn(bc(w[3]), pk(ym[2], ym[3]), hi);
-    lo = __ffma2_rn(bc(w[4]), pk(yp[0], yp[1]), lo);
-    hi = __ffma2_rn(bc(w[4]), pk(yp[2], yp[3]), hi);
-    lo = __ffma2_rn(bc(w[5]), pk(zm[0], zm[1]), lo);
-    hi = __ffma2_rn(bc(w[5]), pk(zm[2], zm[3]), hi);
-    lo = __ffma2_rn(bc(w[6]), pk(zp[0], zp[1]), lo);
-    hi = __ffma2_rn(bc(w[6]), pk(zp[2], zp[3]), hi);
-    d[0] = lo.x; d[1] = lo.y; d[2] = hi.x; d[3] = hi.y;
-}
-
-// z[i] = fma(a, x[i], y[i]) over a vector (packed for FP32).
+// Elementwise helpers over a thread's vector: z = fma(a, x, y), z = x + y, z = a * x.
 template <typename T>
 __device__ __forceinline__ void vfma(T (&z)[VecT<T>::V], T a, const T (&x)[VecT<T>::V],
                                      const T (&y)[VecT<T>::V])
 {
 #pragma unroll
     for (int i = 0; i < VecT<T>::V; ++i) z[i] = fma(a, x[i], y[i]);
-}
-template <>
-__device__ __forceinline__ void vfma<float>(float (&z)[4], float a, const float (&x)[4],
-                                            const float (&y)[4])
-{
-    const float2 lo = __ffma2_rn(bc(a), pk(x[0], x[1]), pk(y[0], y[1]));
-    const float2 hi = __ffma2_rn(bc(a), pk(x[2], x[3]), pk(y[2], y[3]));
-    z[0] = lo.x; z[1] = lo.y; z[2] = hi.x; z[3] = hi.y;
 }
 // z[i] = x[i] + y[i]
 template <typename T>
@@ -214,26 +170,12 @@ __device__ __forceinline__ void vadd(T (&z)[VecT<T>::V], const T (&x)[VecT<T>::V
 #pragma unroll
     for (int i = 0; i < VecT<T>::V; ++i) z[i] = x[i] + y[i];
 }
-template <>
-__device__ __forceinline__ void vadd<float>(float (&z)[4], const float (&x)[4], const float (&y)[4])
-{
-    const float2 lo = __fadd2_rn(pk(x[0], x[1]), pk(y[0], y[1]));
-    const float2 hi = __fadd2_rn(pk(x[2], x[3]), pk(y[2], y[3]));
-    z[0] = lo.x; z[1] = lo.y; z[2] = hi.x; z[3] = hi.y;
-}
 // z[i] = a * x[i]
 template <typename T>
 __device__ __forceinline__ void vmul(T (&z)[VecT<T>::V], T a, const T (&x)[VecT<T>::V])
 {
 #pragma unroll
     for (int i = 0; i < VecT<T>::V; ++i) z[i] = a * x[i];
-}
-template <>
-__device__ __forceinline__ void vmul<float>(float (&z)[4], float a, const float (&x)[4])
-{
-    const float2 lo = __fmul2_rn(bc(a), pk(x[0], x[1]));
-    const float2 hi = __fmul2_rn(bc(a), pk(x[2], x[3]));
-    z[0] = lo.x; z[1] = lo.y; z[2] = hi.x; z[3] = hi.y;
 }
 
 // Register windows of one thread, indexed by iteration modulo their period:

@@ -28,8 +28,8 @@ def test_binding_names_match_header():
 
 
 def test_config_struct_layout_matches_header():
-    # parareal_config: 2 ints, 3 doubles, int, 3 doubles, 3 doubles, 4 ints (with padding)
-    assert ctypes.sizeof(native.Config) == 4 + 4 + 8 * 3 + 8 + 8 * 3 + 8 * 3 + 4 * 4
+    # parareal_config: 2 ints, 3 doubles, int (+pad), 3 doubles, 3 doubles, 5 ints (+pad)
+    assert ctypes.sizeof(native.Config) == 4 + 4 + 8 * 3 + 8 + 8 * 3 + 8 * 3 + 4 * 5 + 4
 
 
 def test_stability_precheck_flags_the_literal_unstable_fine_step():
