@@ -376,6 +376,53 @@ def run_fp64_32(args):
     return 0
 
 
+def paper_exact(n, t, nu0, nu_amp, nu_omega):
+    """u(x, t) = a(t) u0(x - t (1, 1, 1)) with u0 = sin sin sin and
+    a(t) = exp(-12 pi^2 int_0^t nu), the closed-form solution of Sec. 3."""
+    import numpy as np
+    integral = nu0 * t if nu_omega == 0.0 else nu0 * t + nu0 * nu_amp * (1.0 - np.cos(nu_omega * t)) / nu_omega
+    s = np.sin(2 * np.pi * (np.arange(n) / n - t))
+    return np.exp(-12.0 * np.pi ** 2 * integral) * s[:, None, None] * s[None, :, None] * s[None, None, :]
+
+
+def run_paper_faithful(args):
+    """The paper's own configuration (Sec. 3.1) at its size: 128^3 FP64, F = RK4
+    with fourth-order differences at T/2^15, G = forward Euler / upwind at
+    T/2^11, nu frozen: eps_fine, eps_coarse, d^k for k <= 4 with N_p = --slices,
+    times of the serial fine run and of each Parareal iteration count."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1409_8563_gb300 import configs, native
+    out = {"workload": "paper_faithful", "n": 128, "n_slices": args.slices, "runs": {}}
+    for omega in (0.0, 100.0):
+        cfg, u0 = configs.paper_faithful(n=128, n_slices=args.slices, omega=omega)
+        ctx = native.Parareal(cfg)
+        u = torch.from_numpy(u0).cuda()
+        exact = paper_exact(128, cfg.T, cfg.nu0, cfg.nu_amp, cfg.nu_omega)
+        err = lambda f: float(np.max(np.abs(f - exact)) / np.max(np.abs(exact)))
+        res = torch.empty_like(u)
+        ctx.set_problem(u)
+        serial_ms, _ = _timed(lambda: ctx.serial_fine(res, as_reference=True))
+        eps_fine = err(res.cpu().numpy())
+        ctx.set_problem(u)
+        coarse_ms, _ = _timed(lambda: ctx.coarse_sweep(0, cfg.n_slices, chain=True))
+        ctx.get_slice(cfg.n_slices, res)
+        eps_coarse = err(res.cpu().numpy())
+        ctx.set_problem(u)
+        k_max = min(4, cfg.n_slices)
+        par_ms, (k, h) = _timed(lambda: ctx.iterate(k_max, 0.0, native.STOP_NONE))
+        out["runs"][f"omega={omega:g}"] = {
+            "eps_fine": eps_fine, "eps_coarse": eps_coarse, "defects": [float(x) for x in h[:, 2]],
+            "serial_fine_ms": serial_ms, "coarse_chain_ms": coarse_ms,
+            f"parareal_{k_max}_iterations_ms": par_ms,
+            "fine_glups_serial": 128 ** 3 * 2 ** 15 / serial_ms / 1e6}
+        ctx.close()
+    print(json.dumps(out))
+    return 0
+
+
 def run_learned_128(args):
     """128^3, N = 32: learned coarse propagator (trained here on pairs the
     fine solver generates) vs stencil coarse propagator vs shift only vs
@@ -496,9 +543,17 @@ def run_fine_sweep(args):
     ctx.set_problem(u)
     for s in range(1, S + 1):
         ctx.set_slice(s, u)
-    ctx.fine_sweep(0, S)   # warm-up launch; the second sweep is the one to capture
-    ms, _ = _timed(lambda: ctx.fine_sweep(0, S), 1)
-    print(json.dumps({"workload": "fine_sweep", "slices": S, "steps": steps, "ms": ms,
+    ctx.fine_sweep(0, S)   # warm-up launches; the next sweep is the one to capture
+    ctx.profile(True)
+    for _ in range(max(args.steps, 1)):
+        ctx.fine_sweep(0, S)
+    fine_ms, launches, nbytes = ctx.profile_read()
+    ctx.profile(False)
+    per_launch = fine_ms / max(launches, 1)
+    print(json.dumps({"workload": "fine_sweep", "slices": S, "rk4_steps_per_sweep": steps,
+                      "sweeps": max(args.steps, 1), "launch_ms": per_launch,
+                      "glups": S * n ** 3 / per_launch / 1e6,
+                      "gbs_algorithmic": nbytes / launches / per_launch / 1e6,
                       "launch_shape": ctx.launch_shape()[0]}))
     ctx.close()
     return 0
@@ -513,7 +568,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="fp32_256",
-                    choices=["fp32_256", "fp64_32", "learned_128", "batch64", "fine_sweep"])
+                    choices=["fp32_256", "fp64_32", "learned_128", "batch64", "fine_sweep",
+                             "paper_faithful"])
     ap.add_argument("--slices", type=int, default=8)
     ap.add_argument("--tile", default=None, help="fine_sweep: fused tile 'tx,ty,zchunk' instead of autotuning")
     ap.add_argument("--n-ics", type=int, default=63)
@@ -531,6 +587,8 @@ def main():
         return run_batch64(args)
     if args.workload == "fine_sweep":
         return run_fine_sweep(args)
+    if args.workload == "paper_faithful":
+        return run_paper_faithful(args)
     return run(args)
 
 

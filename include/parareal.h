@@ -69,10 +69,21 @@ enum { PARAREAL_NU_STAGE = 0, PARAREAL_NU_FROZEN = 1 };
 
 /* Coarse propagator kinds. */
 enum {
-    PARAREAL_COARSE_STENCIL = 0,  /* RK4 on the (coarsened) grid */
+    PARAREAL_COARSE_STENCIL = 0,  /* RK4 on the (coarsened) grid, 7-point / centred operator */
     PARAREAL_COARSE_LEARNED = 1,  /* shift + convolution net (parareal_set_coarse_model) */
-    PARAREAL_COARSE_SHIFT = 2     /* periodic integer shift only (the net set to zero) */
+    PARAREAL_COARSE_SHIFT = 2,    /* periodic integer shift only (the net set to zero) */
+    PARAREAL_COARSE_EULER_UPWIND = 3  /* the paper's coarse propagator (Sec. 3.1, Algorithm 2):
+                                         forward Euler at dt_coarse, 7-point Laplacian, first-order
+                                         upwind advection, nu at the step start, same grid
+                                         (coarse_factor must be 1) */
 };
+
+/* Spatial operator of the fine propagator F (always classical RK4 in time):
+ * C2 = 7-point Laplacian and centred first differences (Sec. 2.3);
+ * C4 = fourth-order centred differences, (-1,16,-30,16,-1)/(12h^2) and
+ *      (1,-8,0,8,-1)/(12h) per axis, the paper's fine operator (Sec. 3.1).
+ *      C4 runs on the per-stage kernels (no fused path). */
+enum { PARAREAL_SCHEME_C2 = 0, PARAREAL_SCHEME_C4 = 1 };
 
 /* Stopping rules for parareal_iterate. */
 enum {
@@ -104,6 +115,7 @@ typedef struct {
     int coarse_kind;       /* PARAREAL_COARSE_* */
     int allow_unstable;    /* nonzero: stability pre-check failures become a warning */
     int learned_skip;      /* PARAREAL_SKIP_*: the skip path of the learned propagator */
+    int fine_scheme;       /* PARAREAL_SCHEME_*: spatial operator of F */
 } parareal_config;
 
 /* Skip path of the learned coarse propagator (coarse_kind LEARNED / SHIFT):
@@ -122,9 +134,11 @@ parareal_status parareal_create(const parareal_config *cfg, void *cuda_stream,
 /* Stability pre-check without allocation: the largest per-step amplification
  * max |R(dt lambda(k))| over all Fourier modes k of the fine and coarse grids
  * and over nu in [nu0(1-|amp|), nu0(1+|amp|)], where R is the RK4 polynomial
- * and lambda the symbol of the 7-point/centred operator.  growth[0] = fine,
- * growth[1] = coarse (stencil G only, else 0).  Returns E_UNSTABLE when either
- * exceeds 1 + 1e-12 (the per-step value is still written). */
+ * (1 + z for forward Euler) and lambda the symbol of the operator (the fine
+ * scheme for F; 7-point/centred for the stencil G, 7-point/upwind for the
+ * Euler G).  growth[0] = fine, growth[1] = coarse (stencil or Euler G, else
+ * 0).  Returns E_UNSTABLE when either exceeds 1 + 1e-12 (the per-step value is
+ * still written). */
 parareal_status parareal_stability(const parareal_config *cfg, double *growth2);
 
 /* Set u0 = U[0] (Algorithm 1, "Data: initial condition") and reset the

@@ -26,7 +26,8 @@ import math
 import numpy as np
 
 from . import inputs
-from .native import (COARSE_STENCIL, F32, F64, NU_FROZEN, NU_STAGE, Config, stability)
+from .native import (COARSE_EULER_UPWIND, COARSE_STENCIL, F32, F64, NU_FROZEN, NU_STAGE, SCHEME_C4,
+                     Config, stability)
 
 NU_BASE = dict(nu0=0.01, nu_amp=0.5, nu_omega=2 * math.pi)
 
@@ -73,6 +74,20 @@ def paper_128(omega=100.0):
     cfg = Config.make(128, 32, T, T / 2 ** 15, T / 2 ** 11, 1, fine_dtype=F64, nu0=0.1,
                       nu_amp=0.5, nu_omega=omega, nu_mode=NU_FROZEN, allow_unstable=1)
     return cfg, inputs.paper_ic(128)
+
+
+def paper_faithful(n=128, n_slices=8, omega=0.0, fine_log2=15, coarse_log2=11, dtype=F64,
+                   a=(1.0, 1.0, 1.0)):
+    """The paper's own configuration (Sec. 3.1): T = 0.1, nu0 = 0.1,
+    nu(t) = nu0 (1 + 0.5 sin(omega t)) frozen at the step start, a = (1, 1, 1);
+    F = RK4 with fourth-order centred differences at T/2^fine_log2, G = forward
+    Euler with upwind advection at T/2^coarse_log2 on the same grid (Algorithm 2);
+    u0 = sin(2 pi x) sin(2 pi y) sin(2 pi z)."""
+    T = 0.1
+    cfg = Config.make(n, n_slices, T, T / 2 ** fine_log2, T / 2 ** coarse_log2, 1, a=a, nu0=0.1,
+                      nu_amp=0.5, nu_omega=omega, fine_dtype=dtype, nu_mode=NU_FROZEN,
+                      coarse_kind=COARSE_EULER_UPWIND, fine_scheme=SCHEME_C4)
+    return cfg, inputs.paper_ic(n)
 
 
 def small(n=32, n_slices=4, dtype=F64, r=1, nf=32, nc=4, seed=0, ic="spectral"):

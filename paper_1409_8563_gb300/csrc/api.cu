@@ -48,26 +48,46 @@ static bool is_integer_ratio(double a, double b, long long *q)
     return true;
 }
 
-// Largest |R(dt lambda)| over Fourier modes and sampled nu, R the RK4
-// polynomial, lambda the symbol of the 7-point / centred operator.
-static double rk4_growth(int n, double dt, const double a[3], double nu_lo, double nu_hi)
+// Largest |R(dt lambda)| over Fourier modes and sampled nu: R the RK4
+// polynomial (rk4) or 1 + z (forward Euler), lambda = nu L(k) + D(k) the
+// symbol of the operator op on the periodic grid (every Fourier mode is an
+// eigenvector of these circulant stencils).
+static double step_growth(bool rk4, int op, int n, double dt, const double a[3], double nu_lo,
+                          double nu_hi)
 {
     const int stride = n <= 64 ? 1 : n / 64;
-    std::vector<double> L1(n), S1(n);
+    using cplx = std::complex<double>;
+    std::vector<double> L1(n);
+    std::vector<cplx> D1[3];
+    for (int ax = 0; ax < 3; ++ax) D1[ax].resize(n);
+    const double hn = (double)n;   // 1/h
     for (int k = 0; k < n; ++k) {
         const double th = 2.0 * M_PI * k / n;
-        L1[k] = (2.0 * std::cos(th) - 2.0) * n * (double)n;
-        S1[k] = std::sin(th) * n;
+        const double c1 = std::cos(th), s1 = std::sin(th), c2 = std::cos(2 * th), s2 = std::sin(2 * th);
+        // second difference per axis
+        L1[k] = (op == OP_C4 ? (-2.0 * c2 + 32.0 * c1 - 30.0) / 12.0 : 2.0 * c1 - 2.0) * hn * hn;
+        for (int ax = 0; ax < 3; ++ax) {
+            // symbol of -a d/dx as discretised
+            if (op == OP_C4)
+                D1[ax][k] = cplx(0.0, -a[ax] * (8.0 * s1 - s2) / 6.0 * hn);
+            else if (op == OP_C2)
+                D1[ax][k] = cplx(0.0, -a[ax] * s1 * hn);
+            else if (a[ax] > 0.0)   // (u - u_{-1})/h
+                D1[ax][k] = -a[ax] * hn * cplx(1.0 - c1, s1);
+            else                    // (u_{+1} - u)/h
+                D1[ax][k] = -a[ax] * hn * cplx(c1 - 1.0, s1);
+        }
     }
     double g = 0.0;
     const double nus[5] = {nu_lo, 0.75 * nu_lo + 0.25 * nu_hi, 0.5 * (nu_lo + nu_hi),
                            0.25 * nu_lo + 0.75 * nu_hi, nu_hi};
     auto scan = [&](int kx, int ky, int kz) {
         const double L = L1[kx] + L1[ky] + L1[kz];
-        const double D = -(a[0] * S1[kx] + a[1] * S1[ky] + a[2] * S1[kz]);
+        const cplx D = D1[0][kx] + D1[1][ky] + D1[2][kz];
         for (double nu : nus) {
-            const std::complex<double> z(dt * nu * L, dt * D);
-            const std::complex<double> R = 1.0 + z + z * z / 2.0 + z * z * z / 6.0 + z * z * z * z / 24.0;
+            const cplx z = dt * (nu * L + D);
+            const cplx R = rk4 ? 1.0 + z + z * z / 2.0 + z * z * z / 6.0 + z * z * z * z / 24.0
+                               : 1.0 + z;
             g = std::max(g, std::abs(R));
         }
     };
@@ -91,7 +111,9 @@ static parareal_status validate(const parareal_config *cfg, long long *Nf, long 
     }
     if (cfg->fine_dtype != PARAREAL_F32 && cfg->fine_dtype != PARAREAL_F64) { *msg = "fine_dtype"; return PARAREAL_E_INVALID; }
     if (cfg->nu_mode != PARAREAL_NU_STAGE && cfg->nu_mode != PARAREAL_NU_FROZEN) { *msg = "nu_mode"; return PARAREAL_E_INVALID; }
-    if (cfg->coarse_kind < PARAREAL_COARSE_STENCIL || cfg->coarse_kind > PARAREAL_COARSE_SHIFT) { *msg = "coarse_kind"; return PARAREAL_E_INVALID; }
+    if (cfg->coarse_kind < PARAREAL_COARSE_STENCIL || cfg->coarse_kind > PARAREAL_COARSE_EULER_UPWIND) { *msg = "coarse_kind"; return PARAREAL_E_INVALID; }
+    if (cfg->coarse_kind == PARAREAL_COARSE_EULER_UPWIND && cfg->coarse_factor != 1) { *msg = "the Euler/upwind coarse propagator runs on the fine grid (coarse_factor 1)"; return PARAREAL_E_INVALID; }
+    if (cfg->fine_scheme != PARAREAL_SCHEME_C2 && cfg->fine_scheme != PARAREAL_SCHEME_C4) { *msg = "fine_scheme"; return PARAREAL_E_INVALID; }
     if (cfg->learned_skip != PARAREAL_SKIP_SHIFT && cfg->learned_skip != PARAREAL_SKIP_STENCIL) { *msg = "learned_skip"; return PARAREAL_E_INVALID; }
     const double slice = cfg->T / cfg->n_slices;
     if (!is_integer_ratio(slice, cfg->dt_fine, Nf)) { *msg = "T/(n_slices dt_fine) must be an integer"; return PARAREAL_E_INVALID; }
@@ -108,11 +130,13 @@ extern "C" parareal_status parareal_stability(const parareal_config *cfg, double
     if (s != PARAREAL_OK) return fail(nullptr, s, msg);
     const double lo = cfg->nu0 * (1.0 - std::fabs(cfg->nu_amp));
     const double hi = cfg->nu0 * (1.0 + std::fabs(cfg->nu_amp));
-    const double gf = rk4_growth(cfg->n, cfg->dt_fine, cfg->a, lo, hi);
-    const double gc = (cfg->coarse_kind == PARAREAL_COARSE_STENCIL ||
-                       cfg->learned_skip == PARAREAL_SKIP_STENCIL)
-                          ? rk4_growth(cfg->n / cfg->coarse_factor, cfg->dt_coarse, cfg->a, lo, hi)
-                          : 0.0;
+    const double gf = step_growth(true, cfg->fine_scheme == PARAREAL_SCHEME_C4 ? OP_C4 : OP_C2,
+                                  cfg->n, cfg->dt_fine, cfg->a, lo, hi);
+    double gc = 0.0;
+    if (cfg->coarse_kind == PARAREAL_COARSE_EULER_UPWIND)
+        gc = step_growth(false, OP_UPWIND, cfg->n, cfg->dt_coarse, cfg->a, lo, hi);
+    else if (cfg->coarse_kind == PARAREAL_COARSE_STENCIL || cfg->learned_skip == PARAREAL_SKIP_STENCIL)
+        gc = step_growth(true, OP_C2, cfg->n / cfg->coarse_factor, cfg->dt_coarse, cfg->a, lo, hi);
     if (growth2) { growth2[0] = gf; growth2[1] = gc; }
     if (gf > 1.0 + 1e-12 || gc > 1.0 + 1e-12) {
         g_create_error = "stability pre-check: per-step growth fine " + std::to_string(gf) +
@@ -172,9 +196,12 @@ static parareal_status prof_begin(parareal_ctx *c)
 template <typename T>
 parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, int first_slice, int count,
                           long long nsteps, double dt, int path, int tx, int ty, int zc, T *ws1,
-                          T *ws2, T *ws3, int slice_stride)
+                          T *ws2, T *ws3, int slice_stride, int op)
 {
+    if (path == PATH_FUSED && op != OP_C2)
+        return fail(c, PARAREAL_E_INVALID, "the fused RK4 kernel implements the 7-point operator only");
     StepArgs a{};
+    a.op = op;
     a.n = m;
     a.P = (long long)m * m * m;
     a.count = count;
@@ -221,10 +248,53 @@ parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, int first
 
 template parareal_status rk4_batch<float>(parareal_ctx *, int, const float *, float *, int, int,
                                           long long, double, int, int, int, int, float *, float *,
-                                          float *, int);
+                                          float *, int, int);
 template parareal_status rk4_batch<double>(parareal_ctx *, int, const double *, double *, int, int,
                                            long long, double, int, int, int, int, double *,
-                                           double *, double *, int);
+                                           double *, double *, int, int);
+
+template <typename T>
+parareal_status euler_batch(parareal_ctx *c, int m, const T *in, T *out, int first_slice,
+                            int count, long long nsteps, double dt, int op, T *ws1, T *ws2)
+{
+    StepArgs a{};
+    a.op = op;
+    a.n = m;
+    a.P = (long long)m * m * m;
+    a.count = count;
+    a.first_slice = first_slice;
+    a.slice_stride = 1;
+    a.steps_per_slice = nsteps;
+    a.dt = dt;
+    for (int d = 0; d < 3; ++d) a.a[d] = c->cfg.a[d];
+    a.nu0 = c->cfg.nu0;
+    a.nu_amp = c->cfg.nu_amp;
+    a.nu_omega = c->cfg.nu_omega;
+    a.frozen = 1;
+    if (nsteps == 0) {
+        if (in != out)
+            CK(cudaMemcpyAsync(out, in, (size_t)count * a.P * sizeof(T), cudaMemcpyDeviceToDevice, c->st));
+        return PARAREAL_OK;
+    }
+    // ping-pong between the two workspaces, the last step written to out; a
+    // step never reads the buffer it writes
+    const T *src = in;
+    if (in == out || in == ws1) {
+        CK(cudaMemcpyAsync(ws2, in, (size_t)count * a.P * sizeof(T), cudaMemcpyDeviceToDevice, c->st));
+        src = ws2;
+    }
+    for (long long j = 0; j < nsteps; ++j) {
+        T *dst = (j == nsteps - 1) ? out : ((j & 1) ? ws2 : ws1);
+        a.j = j;
+        LK(launch_rk4_stage<T>(a, 0, src, nullptr, dst, nullptr, c->st));
+        src = dst;
+    }
+    return PARAREAL_OK;
+}
+template parareal_status euler_batch<float>(parareal_ctx *, int, const float *, float *, int, int,
+                                            long long, double, int, float *, float *);
+template parareal_status euler_batch<double>(parareal_ctx *, int, const double *, double *, int,
+                                             int, long long, double, int, double *, double *);
 
 // ------------------------------------------------------------ propagators
 
@@ -246,7 +316,7 @@ static parareal_status fine_sweep_t(parareal_ctx *c, int first, int count)
     T *ws1 = static_cast<T *>(c->wA), *ws2 = static_cast<T *>(c->wB), *ws3 = static_cast<T *>(c->wC);
     if (c->fine_path == PATH_FUSED && in == ws1) std::swap(ws1, ws3);
     return rk4_batch<T>(c, c->n, in, Fv, first, count, c->Nf, c->cfg.dt_fine, c->fine_path,
-                        c->fine_tx, c->fine_ty, c->fine_zc, ws1, ws2, ws3);
+                        c->fine_tx, c->fine_ty, c->fine_zc, ws1, ws2, ws3, 1, c->fine_op);
 }
 
 // The stencil coarse propagator of slice s on the fine grid, in FP64: RK4 on
@@ -293,6 +363,19 @@ static parareal_status coarse_apply_t(parareal_ctx *c, const double *Uin, int s,
 {
     T *cA = static_cast<T *>(c->cA), *cB = static_cast<T *>(c->cB), *cC = static_cast<T *>(c->cC),
       *cD = static_cast<T *>(c->cD);
+    if (c->cfg.coarse_kind == PARAREAL_COARSE_EULER_UPWIND) {
+        // forward Euler / upwind (Algorithm 2) on the fine grid, FP64 out
+        if (std::is_same<T, float>::value) {
+            LK(launch_convert_f64_to_f32(Uin, reinterpret_cast<float *>(cA), c->P, c->st));
+            parareal_status ps = euler_batch<T>(c, c->n, cA, cB, s, 1, c->Nc, c->cfg.dt_coarse,
+                                                OP_UPWIND, cC, cD);
+            if (ps != PARAREAL_OK) return ps;
+            LK(launch_convert_f32_to_f64(reinterpret_cast<const float *>(cB), static_cast<double *>(out), c->P, c->st));
+            return PARAREAL_OK;
+        }
+        return euler_batch<T>(c, c->n, reinterpret_cast<const T *>(Uin), static_cast<T *>(out), s, 1,
+                              c->Nc, c->cfg.dt_coarse, OP_UPWIND, cB, cC);
+    }
     if (c->cfg.coarse_kind != PARAREAL_COARSE_STENCIL) {
         if (c->cfg.learned_skip == PARAREAL_SKIP_STENCIL) {
             // the net corrects the stencil propagator's output on the fine grid
@@ -484,6 +567,11 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
         delete c;
         return fail(nullptr, PARAREAL_E_INVALID, "unsupported launch shape override");
     }
+    c->fine_op = cfg->fine_scheme == PARAREAL_SCHEME_C4 ? OP_C4 : OP_C2;
+    if (c->fine_op != OP_C2) {
+        // the fused kernel implements the 7-point operator only
+        c->fine_path = c->ser_path = PATH_STAGED;
+    }
 
     auto alloc = [&](void **p, size_t bytes) -> bool {
         if (cudaMalloc(p, bytes) != cudaSuccess) { cudaGetLastError(); *p = nullptr; return false; }
@@ -520,7 +608,7 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
         parareal_destroy(c);
         return fail(nullptr, PARAREAL_E_CUDA, "memset failed");
     }
-    if (cfg->coarse_kind != PARAREAL_COARSE_STENCIL) {
+    if (cfg->coarse_kind == PARAREAL_COARSE_LEARNED || cfg->coarse_kind == PARAREAL_COARSE_SHIFT) {
         parareal_status ns = net_setup(c);
         if (ns != PARAREAL_OK) {
             const std::string msg = c->err;
@@ -770,7 +858,8 @@ extern "C" parareal_status parareal_serial_fine(parareal_ctx *c, void *dst, int 
         for (int n = 0; n < c->N && s == PARAREAL_OK; ++n) {
             s = rk4_batch<double>(c, c->n, cur, Fv1, n, 1, c->Nf, c->cfg.dt_fine, c->ser_path,
                                   c->ser_tx, c->ser_ty, c->ser_zc, static_cast<double *>(c->wA),
-                                  static_cast<double *>(c->wB), static_cast<double *>(c->wC));
+                                  static_cast<double *>(c->wB), static_cast<double *>(c->wC), 1,
+                                  c->fine_op);
             if (s == PARAREAL_OK) CK(cudaMemcpyAsync(cur, Fv1, P * 8, cudaMemcpyDeviceToDevice, c->st));
         }
         if (s != PARAREAL_OK) return s;
@@ -782,7 +871,8 @@ extern "C" parareal_status parareal_serial_fine(parareal_ctx *c, void *dst, int 
         for (int n = 0; n < c->N && s == PARAREAL_OK; ++n) {
             s = rk4_batch<float>(c, c->n, cur, Fv1, n, 1, c->Nf, c->cfg.dt_fine, c->ser_path,
                                  c->ser_tx, c->ser_ty, c->ser_zc, static_cast<float *>(c->wA),
-                                 static_cast<float *>(c->wB), static_cast<float *>(c->wC));
+                                 static_cast<float *>(c->wB), static_cast<float *>(c->wC), 1,
+                                 c->fine_op);
             if (s == PARAREAL_OK) CK(cudaMemcpyAsync(cur, Fv1, P * 4, cudaMemcpyDeviceToDevice, c->st));
         }
         if (s != PARAREAL_OK) return s;
@@ -842,7 +932,7 @@ static parareal_status propagate_t(parareal_ctx *c, int which, const void *src, 
                 CK(cudaMemcpyAsync(tin, in64, P * 8, cudaMemcpyDeviceToDevice, c->st));
             s = rk4_batch<T>(c, c->n, tin, tout, first + f, 1, c->Nf, c->cfg.dt_fine, c->ser_path,
                              c->ser_tx, c->ser_ty, c->ser_zc, static_cast<T *>(c->wA),
-                             static_cast<T *>(c->wB), static_cast<T *>(c->wC));
+                             static_cast<T *>(c->wB), static_cast<T *>(c->wC), 1, c->fine_op);
             if (s != PARAREAL_OK) return s;
             if (std::is_same<T, float>::value)
                 LK(launch_convert_f32_to_f64(reinterpret_cast<const float *>(tout), res64, P, c->st));
@@ -1005,15 +1095,18 @@ extern "C" parareal_status parareal_autotune(parareal_ctx *c, const char *cache_
     CK(cudaMemsetAsync(c->wC, 0, (size_t)c->N * c->P * c->esz, c->st));
     CK(cudaMemsetAsync(c->cA, 0, (size_t)(c->r > 1 ? c->Pc : c->P) * c->esz, c->st));
     double fms = 0.0, cms = 0.0;
-    parareal_status s;
-    if (c->f64)
+    parareal_status s = PARAREAL_OK;
+    if (c->fine_op != OP_C2) {
+        // F runs on the per-stage kernels, which have no launch shape to tune
+    } else if (c->f64)
         s = tune_one<double>(c, cache_path, c->n, c->N, c->cfg.dt_fine, &c->fine_path, &c->fine_tx,
                              &c->fine_ty, &c->fine_zc, &fms);
     else
         s = tune_one<float>(c, cache_path, c->n, c->N, c->cfg.dt_fine, &c->fine_path, &c->fine_tx,
                             &c->fine_ty, &c->fine_zc, &fms);
     if (s != PARAREAL_OK) return s;
-    if (c->N > 1) {
+    if (c->fine_op != OP_C2) {
+    } else if (c->N > 1) {
         // one fine field at a time (serial fine run, propagate)
         double sms = 0.0;
         if (c->f64)

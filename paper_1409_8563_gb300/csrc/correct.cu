@@ -5,9 +5,10 @@
 //
 // G's two outputs enter only through their difference.  A null Fv or gold
 // reads as zero (the start-up chain writes U[n+1] = G(U[n]) this way).  For a coarse-grid G
-// (factor r > 1) the difference of the two coarse results is prolonged
-// (trilinear; a linear map, so P(c_new) - P(c_old) = P(c_new - c_old)) and an
-// unchanged input still gives an exactly zero correction.  Every block also
+// (factor r > 1) the difference of the two coarse results, taken in G's
+// precision, is prolonged (trilinear; a linear map, so P(c_new) - P(c_old) =
+// P(c_new - c_old)) and an unchanged input still gives an exactly zero
+// correction.  Every block also
 // produces partial norms of dU = U^{k+1} - U^k and of U^{k+1}:
 //   {max|dU|, max|U|, sum dU^2, sum U^2, non-finite flag},
 // reduced per block with warp shuffles and then across blocks in a fixed
@@ -118,16 +119,18 @@ correct_kernel(const TF *__restrict__ Fv, const TG *__restrict__ gnew, const TG 
                 dg = (double)gnew[p] - (gold ? (double)gold[p] : 0.0);
             } else {
                 // G's output change on the fine grid: trilinear prolongation
-                // of the difference of the two coarse results (exact in FP64,
-                // then rounded to the coarse precision TG)
+                // of the difference of the two coarse results, taken in the
+                // coarse precision TG (one correctly rounded subtraction per
+                // corner; no FP64 conversions, which run on the narrow FP64
+                // pipe)
                 const int z = (int)(row / n), y = (int)(row - (long long)z * n);
                 int y0, y1, z0, z1;
                 TG wy, wz;
                 lin_weights<TG>(y, r, nc, y0, y1, wy);
                 lin_weights<TG>(z, r, nc, z0, z1, wz);
-                auto dc = [&](int I, int J, int K) {
+                auto dc = [&](int I, int J, int K) -> TG {
                     const long long q = ((long long)K * nc + J) * nc + I;
-                    return (TG)((double)gnew[q] - (gold ? (double)gold[q] : 0.0));
+                    return gold ? gnew[q] - gold[q] : gnew[q];
                 };
                 const TG c00 = fma(wx, dc(x1, y0, z0) - dc(x0, y0, z0), dc(x0, y0, z0));
                 const TG c10 = fma(wx, dc(x1, y1, z0) - dc(x0, y1, z0), dc(x0, y1, z0));

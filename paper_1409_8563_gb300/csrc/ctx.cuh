@@ -65,6 +65,7 @@ struct parareal_ctx {
 
     // launch shapes: the batched fine sweep (N fields), one fine field (serial
     // fine run, propagate) and one coarse field
+    int fine_op = pr::OP_C2;      // operator of F (the fused path needs OP_C2)
     int fine_path = PATH_FUSED, fine_tx = 64, fine_ty = 16, fine_zc = 0;
     int ser_path = PATH_FUSED, ser_tx = 64, ser_ty = 16, ser_zc = 0;
     int coarse_path = PATH_FUSED, coarse_tx = 32, coarse_ty = 8, coarse_zc = 0;
@@ -100,7 +101,13 @@ parareal_status fail(parareal_ctx *c, parareal_status s, const std::string &msg)
 template <typename T>
 parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, int first_slice, int count,
                           long long nsteps, double dt, int path, int tx, int ty, int zc, T *ws1,
-                          T *ws2, T *ws3, int slice_stride = 1);
+                          T *ws2, T *ws3, int slice_stride = 1, int op = pr::OP_C2);
+
+// api.cu: nsteps forward Euler steps (Algorithm 2) of `count` fields with
+// operator op; in may equal out; ws1/ws2 are count*m^3 workspaces.
+template <typename T>
+parareal_status euler_batch(parareal_ctx *c, int m, const T *in, T *out, int first_slice,
+                            int count, long long nsteps, double dt, int op, T *ws1, T *ws2);
 
 // api.cu: one Parareal iteration split into device work and host bookkeeping
 parareal_status iter_enqueue(parareal_ctx *c);

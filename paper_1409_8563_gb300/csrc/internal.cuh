@@ -27,7 +27,16 @@ struct StepArgs {
     double a[3];
     double nu0, nu_amp, nu_omega;
     int frozen;               // nu at step start for all stages
+    int op;                   // OP_*: spatial operator (the fused kernel is OP_C2 only)
 };
+
+// Spatial operators.  OP_C2: 7-point Laplacian, centred first differences.
+// OP_C4: fourth-order centred differences (radius 2, 13 points).  OP_UPWIND:
+// 7-point Laplacian, first-order upwind first differences.
+enum { OP_C2 = 0, OP_C4 = 1, OP_UPWIND = 2 };
+
+// Stencil radius of an operator.
+__host__ __device__ inline int op_radius(int op) { return op == OP_C4 ? 2 : 1; }
 
 // Per-stage 7-point weights of delta = dt * A(nu_s) y:
 // w[0] centre, w[1] x-1, w[2] x+1, w[3] y-1, w[4] y+1, w[5] z-1, w[6] z+1.
@@ -44,6 +53,40 @@ __host__ __device__ inline void stage_weights(double nu, double dt, int n, const
     }
 }
 
+// Weights of delta = dt * A(nu) y for any operator: w[0] centre, then the
+// radius-1 neighbours in the order of stage_weights (x-1, x+1, y-1, y+1, z-1,
+// z+1), then for OP_C4 the radius-2 neighbours in the same order.
+__host__ __device__ inline void op_weights(int op, double nu, double dt, int n, const double a[3],
+                                           double w[13])
+{
+    const double inv_h = (double)n;
+    if (op == OP_C2) {
+        stage_weights(nu, dt, n, a, w);
+        return;
+    }
+    if (op == OP_C4) {
+        const double d = dt * nu * inv_h * inv_h / 12.0;   // dt nu / (12 h^2)
+        w[0] = -90.0 * d;                                  // three axes of -30
+        for (int ax = 0; ax < 3; ++ax) {
+            const double e = dt * a[ax] * inv_h / 12.0;    // dt a / (12 h)
+            w[1 + 2 * ax] = 16.0 * d + 8.0 * e;            // u_{-1}
+            w[2 + 2 * ax] = 16.0 * d - 8.0 * e;            // u_{+1}
+            w[7 + 2 * ax] = -d - e;                        // u_{-2}
+            w[8 + 2 * ax] = -d + e;                        // u_{+2}
+        }
+        return;
+    }
+    // OP_UPWIND: a > 0 differences (u - u_{-1})/h, a < 0 (u_{+1} - u)/h
+    const double d = dt * nu * inv_h * inv_h;
+    w[0] = -6.0 * d;
+    for (int ax = 0; ax < 3; ++ax) {
+        const double e = dt * a[ax] * inv_h;               // dt a / h
+        w[1 + 2 * ax] = d + (e > 0.0 ? e : 0.0);
+        w[2 + 2 * ax] = d - (e < 0.0 ? e : 0.0);
+        w[0] -= (e > 0.0 ? e : -e);
+    }
+}
+
 // ------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return cudaGetLastError().
 
@@ -54,7 +97,9 @@ cudaError_t launch_rk4_fused(const StepArgs &a, const T *in, T *out, int tile_x,
 bool rk4_fused_supported(int dtype, int n, int tile_x, int tile_y);
 cudaError_t configure_rk4_kernels();
 
-// One RK4 stage per launch (no halo recomputation; state kept in HBM/L2).
+// One RK4 stage per launch (no halo recomputation; state kept in HBM/L2),
+// any operator.  Stage 0 is one forward Euler step: ydst = ysrc + dt A ysrc
+// (u and acc unused).
 template <typename T>
 cudaError_t launch_rk4_stage(const StepArgs &a, int stage, const T *ysrc, T *u, T *ydst,
                              T *acc, cudaStream_t st);

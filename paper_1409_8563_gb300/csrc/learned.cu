@@ -188,7 +188,8 @@ static parareal_status stage_batch(parareal_ctx *c, const float *const *us, cons
 static parareal_status need_learned(parareal_ctx *c)
 {
     if (!c) return PARAREAL_E_INVALID;
-    if (c->cfg.coarse_kind == PARAREAL_COARSE_STENCIL || !c->net.master)
+    if ((c->cfg.coarse_kind != PARAREAL_COARSE_LEARNED && c->cfg.coarse_kind != PARAREAL_COARSE_SHIFT) ||
+        !c->net.master)
         return fail(c, PARAREAL_E_STATE, "context was not created with a learned coarse propagator");
     return PARAREAL_OK;
 }
@@ -378,7 +379,7 @@ static parareal_status make_pairs_t(parareal_ctx *c, const float *ics, int n_ics
         }
         if (s != PARAREAL_OK) break;
         s = rk4_batch<T>(c, c->n, st, nx, n, n_ics, c->Nf, c->cfg.dt_fine, c->fine_path, c->fine_tx,
-                         c->fine_ty, c->fine_zc, w1, w2, w3, 0);
+                         c->fine_ty, c->fine_zc, w1, w2, w3, 0, c->fine_op);
         if (s != PARAREAL_OK) break;
         for (int i = 0; i < n_ics && s == PARAREAL_OK; ++i)
             s = emit(nx + (size_t)i * P, pf + ((size_t)i * c->N + n) * Pm);

@@ -154,7 +154,7 @@ __device__ __forceinline__ void stage_delta(T (&d)[VecT<T>::V], const T *__restr
     }
 }
 
-// Elementwise helpers over a thread's vector: z = fma(a, x, y), z = x + y, z = a * x.
+// Elementwise helpers over a thread's vector: z = fma(a, x, y), z = x + y.
 template <typename T>
 __device__ __forceinline__ void vfma(T (&z)[VecT<T>::V], T a, const T (&x)[VecT<T>::V],
                                      const T (&y)[VecT<T>::V])
@@ -170,22 +170,19 @@ __device__ __forceinline__ void vadd(T (&z)[VecT<T>::V], const T (&x)[VecT<T>::V
 #pragma unroll
     for (int i = 0; i < VecT<T>::V; ++i) z[i] = x[i] + y[i];
 }
-// z[i] = a * x[i]
-template <typename T>
-__device__ __forceinline__ void vmul(T (&z)[VecT<T>::V], T a, const T (&x)[VecT<T>::V])
-{
-#pragma unroll
-    for (int i = 0; i < VecT<T>::V; ++i) z[i] = a * x[i];
-}
 
 // Register windows of one thread, indexed by iteration modulo their period:
-// u of iteration j in U[j % 4], y2/y3/y4 produced at iteration j in
-// Y*[j % 3], the RK4 increment sum started at iteration j in A[j % 4].
+// u of iteration j in U[j % 4], y2 produced at iteration j in Y2[j % 4],
+// y3/y4 produced at iteration j in Y3[j % 3] / Y4[j % 3].  The step's result
+// is formed from the stage values of its plane,
+//   u' = u + ((y2 - u) + 2 (y3 - u) + (y4 - u)) / 3 + d4 / 6,
+// which equals u + d1/6 + d2/3 + d3/3 + d4/6 (y2 = u + d1/2, y3 = u + d2/2,
+// y4 = u + d3) and needs no running increment sum; the differences y - u
+// are exact where y is within a factor 2 of u.
 template <typename T>
 struct FusedRegs {
     T U[4][VecT<T>::V];
-    T Y2[3][VecT<T>::V], Y3[3][VecT<T>::V], Y4[3][VecT<T>::V];
-    T A[4][VecT<T>::V];
+    T Y2[4][VecT<T>::V], Y3[3][VecT<T>::V], Y4[3][VecT<T>::V];
 };
 
 // Everything one z-iteration needs besides the registers.
@@ -231,32 +228,36 @@ __device__ __forceinline__ void fused_step(FusedIter<T> &I, FusedRegs<T> &R, con
     T *En = I.eplanes + ((PH + 1) & 1) * 6 * EL;
 
     T d[V];
-    T y2n[V] = {}, y3n[V] = {}, y4n[V] = {}, accn[V] = {};
+    T y2n[V] = {}, y3n[V] = {}, y4n[V] = {};
     // stage 1 at the plane of iteration it-1
     if (I.act1) {
         stage_delta<T>(d, Su, Eu, EL, L, R.U[(PH + 3) % 4], R.U[(PH + 2) % 4], un, w1);
         vfma<T>(y2n, hf, d, R.U[(PH + 3) % 4]);
-        vmul<T>(accn, c6, d);
     }
     // stage 2 at the plane of iteration it-2
     if (I.act2) {
-        stage_delta<T>(d, Sc, Ec, EL, L, R.Y2[(PH + 2) % 3], R.Y2[(PH + 1) % 3], y2n, w2);
+        stage_delta<T>(d, Sc, Ec, EL, L, R.Y2[(PH + 3) % 4], R.Y2[(PH + 2) % 4], y2n, w2);
         vfma<T>(y3n, hf, d, R.U[(PH + 2) % 4]);
-        vfma<T>(R.A[(PH + 3) % 4], c3, d, R.A[(PH + 3) % 4]);
     }
     // stage 3 at the plane of iteration it-3
     if (I.act3) {
         stage_delta<T>(d, Sc + PL, Ec + 2 * EL, EL, L, R.Y3[(PH + 2) % 3], R.Y3[(PH + 1) % 3], y3n, w2);
         vadd<T>(y4n, R.U[(PH + 1) % 4], d);
-        vfma<T>(R.A[(PH + 2) % 4], c3, d, R.A[(PH + 2) % 4]);
     }
     // stage 4 at the plane of iteration it-4: the finished step
     if (I.act4) {
-        stage_delta<T>(d, Sc + 2 * PL, Ec + 4 * EL, EL, L, R.Y4[(PH + 2) % 3], R.Y4[(PH + 1) % 3], y4n, w4);
+        const T(&u4)[V] = R.U[PH % 4];
+        const T(&y4c)[V] = R.Y4[(PH + 2) % 3];
+        stage_delta<T>(d, Sc + 2 * PL, Ec + 4 * EL, EL, L, y4c, R.Y4[(PH + 1) % 3], y4n, w4);
         if (I.owner && it >= 8) {
-            T o[V], inc[V];
-            vfma<T>(inc, c6, d, R.A[(PH + 1) % 4]);
-            vadd<T>(o, R.U[PH % 4], inc);
+            const T(&y2c)[V] = R.Y2[(PH + 1) % 4];
+            const T(&y3c)[V] = R.Y3[(PH + 1) % 3];
+            T o[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const T s = fma((T)2, y3c[i] - u4[i], (y2c[i] - u4[i]) + (y4c[i] - u4[i]));
+                o[i] = fma(c3, s, fma(c6, d[i], u4[i]));
+            }
             stv<T>(I.dst + I.ooff, o);
         }
     }
@@ -274,10 +275,9 @@ __device__ __forceinline__ void fused_step(FusedIter<T> &I, FusedRegs<T> &R, con
 #pragma unroll
     for (int i = 0; i < V; ++i) {
         R.U[PH % 4][i] = un[i];
-        R.Y2[PH % 3][i] = y2n[i];
+        R.Y2[PH % 4][i] = y2n[i];
         R.Y3[PH % 3][i] = y3n[i];
         R.Y4[PH % 3][i] = y4n[i];
-        R.A[PH % 4][i] = accn[i];
     }
 }
 
@@ -384,9 +384,9 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
 #pragma unroll
     for (int i = 0; i < V; ++i) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) R.U[k][i] = R.A[k][i] = (T)0;
+        for (int k = 0; k < 4; ++k) R.U[k][i] = R.Y2[k][i] = (T)0;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) R.Y2[k][i] = R.Y3[k][i] = R.Y4[k][i] = (T)0;
+        for (int k = 0; k < 3; ++k) R.Y3[k][i] = R.Y4[k][i] = (T)0;
     }
     for (int base = 0; base < I.n_it; base += 12) {
         fused_step<T, TX, TY, 0>(I, R, L, base + 0, w1, w2, w4);
@@ -479,40 +479,52 @@ template cudaError_t launch_rk4_fused<double>(const StepArgs &, const double *, 
 
 // ------------------------------------------------------------ staged RK4
 
-template <typename T>
+// One stage of one step, one point per thread, any operator of radius R
+// (weights from op_weights).  Stages 1-4 are the RK4 stages of the file
+// header (ysrc = y_s, u = the step's start value, acc = running increment
+// sum); stage 0 is a forward Euler step ydst = ysrc + dt A(nu(t)) ysrc.
+template <typename T, int R>
 __global__ void __launch_bounds__(256)
 rk4_stage_kernel(StepArgs a, int stage, const T *__restrict__ ysrc, T *__restrict__ u,
                  T *__restrict__ ydst, T *__restrict__ acc)
 {
-    __shared__ T s_w[7];
+    constexpr int NW = 1 + 6 * R;
+    __shared__ T s_w[NW];
     const int f = blockIdx.y;
     if (threadIdx.x == 0) {
         const long long s = (long long)(a.first_slice + f * a.slice_stride) * a.steps_per_slice + a.j;
         const double t = (double)s * a.dt;
-        const double c = (stage == 1 || a.frozen) ? 0.0 : (stage == 4 ? 1.0 : 0.5);
-        double w[7];
-        stage_weights(nu_at(a, t + c * a.dt), a.dt, a.n, a.a, w);
-        for (int k = 0; k < 7; ++k) s_w[k] = (T)w[k];
+        const double c = (stage <= 1 || a.frozen) ? 0.0 : (stage == 4 ? 1.0 : 0.5);
+        double w[13];
+        op_weights(a.op, nu_at(a, t + c * a.dt), a.dt, a.n, a.a, w);
+        for (int k = 0; k < NW; ++k) s_w[k] = (T)w[k];
     }
     __syncthreads();
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.P) return;
     const int n = a.n;
     const int x = (int)(p % n), y = (int)((p / n) % n), z = (int)(p / ((long long)n * n));
-    const long long off = (long long)f * a.P;
-    const T *Y = ysrc + off;
-    const int xm = x ? x - 1 : n - 1, xp = x + 1 < n ? x + 1 : 0;
-    const int ym = y ? y - 1 : n - 1, yp = y + 1 < n ? y + 1 : 0;
-    const int zm = z ? z - 1 : n - 1, zp = z + 1 < n ? z + 1 : 0;
-    const long long row = (long long)z * n * n + (long long)y * n;
+    const T *Y = ysrc + (long long)f * a.P;
+    const long long nn = (long long)n * n;
+    // periodic neighbour index at distance k (|k| <= R < n) along one axis
+    auto wrap = [n](int i, int k) { i += k; return i < 0 ? i + n : (i >= n ? i - n : i); };
+    const long long row = (long long)z * nn + (long long)y * n;
     T d = s_w[0] * Y[row + x];
-    d = fma(s_w[1], Y[row + xm], d);
-    d = fma(s_w[2], Y[row + xp], d);
-    d = fma(s_w[3], Y[(long long)z * n * n + (long long)ym * n + x], d);
-    d = fma(s_w[4], Y[(long long)z * n * n + (long long)yp * n + x], d);
-    d = fma(s_w[5], Y[(long long)zm * n * n + (long long)y * n + x], d);
-    d = fma(s_w[6], Y[(long long)zp * n * n + (long long)y * n + x], d);
-    const long long q = off + p;
+#pragma unroll
+    for (int r = 1; r <= R; ++r) {
+        const int b = 1 + 6 * (r - 1);
+        d = fma(s_w[b + 0], Y[row + wrap(x, -r)], d);
+        d = fma(s_w[b + 1], Y[row + wrap(x, r)], d);
+        d = fma(s_w[b + 2], Y[(long long)z * nn + (long long)wrap(y, -r) * n + x], d);
+        d = fma(s_w[b + 3], Y[(long long)z * nn + (long long)wrap(y, r) * n + x], d);
+        d = fma(s_w[b + 4], Y[(long long)wrap(z, -r) * nn + (long long)y * n + x], d);
+        d = fma(s_w[b + 5], Y[(long long)wrap(z, r) * nn + (long long)y * n + x], d);
+    }
+    const long long q = (long long)f * a.P + p;
+    if (stage == 0) {
+        ydst[q] = Y[p] + d;
+        return;
+    }
     const T uq = u[q];
     if (stage == 1) {
         ydst[q] = fma((T)0.5, d, uq);
@@ -534,7 +546,10 @@ cudaError_t launch_rk4_stage(const StepArgs &a, int stage, const T *ysrc, T *u, 
 {
     const unsigned bx = (unsigned)((a.P + 255) / 256);
     dim3 grid(bx, (unsigned)a.count);
-    rk4_stage_kernel<T><<<grid, 256, 0, st>>>(a, stage, ysrc, u, ydst, acc);
+    if (op_radius(a.op) == 2)
+        rk4_stage_kernel<T, 2><<<grid, 256, 0, st>>>(a, stage, ysrc, u, ydst, acc);
+    else
+        rk4_stage_kernel<T, 1><<<grid, 256, 0, st>>>(a, stage, ysrc, u, ydst, acc);
     return cudaGetLastError();
 }
 template cudaError_t launch_rk4_stage<float>(const StepArgs &, int, const float *, float *,

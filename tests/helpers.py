@@ -17,9 +17,11 @@ def steps(cfg):
     return int(round(sl / cfg.dt_fine)), int(round(sl / cfg.dt_coarse))
 
 
-def oracle_problem(cfg, n=None):
+def oracle_problem(cfg, n=None, scheme=None):
+    if scheme is None:
+        scheme = core.C4 if getattr(cfg, "fine_scheme", 0) == 1 else core.C2
     return core.Problem(cfg.n if n is None else n, a=tuple(cfg.a), nu0=cfg.nu0,
-                        nu_amp=cfg.nu_amp, nu_omega=cfg.nu_omega, scheme=core.C2)
+                        nu_amp=cfg.nu_amp, nu_omega=cfg.nu_omega, scheme=scheme)
 
 
 def oracle_F(cfg):
@@ -29,7 +31,9 @@ def oracle_F(cfg):
 
 def oracle_G(cfg):
     _, nc = steps(cfg)
-    P = oracle_problem(cfg)
+    if cfg.coarse_kind == 3:   # forward Euler / upwind on the same grid (Algorithm 2)
+        return opr.euler_propagator(oracle_problem(cfg, scheme=core.UPWIND), cfg.dt_coarse, nc)
+    P = oracle_problem(cfg, scheme=core.C2)
     if cfg.coarse_factor == 1:
         return opr.rk4_propagator(P, cfg.dt_coarse, nc, frozen=cfg.nu_mode == 1)
     return opr.coarsened_rk4_propagator(P, cfg.coarse_factor, cfg.dt_coarse, nc,

@@ -1,0 +1,142 @@
+"""GPU path of the paper's own configuration (Sec. 3.1): F is RK4 with
+fourth-order centred differences, G is forward Euler with first-order upwind
+advection and the 7-point Laplacian (Algorithm 2) on the same grid, nu frozen
+at the step start.
+
+Parity against the FP64 oracle at small sizes (relative L2 1e-12 in FP64,
+1e-5 in FP32), then the paper's printed errors at its own size (128^3,
+T = 0.1, dt_F = T/2^15, dt_G = T/2^11): eps_fine, eps_coarse and the defect
+after three iterations (Sec. 3.1, Sec. 3.4.1).
+"""
+import numpy as np
+import pytest
+
+from oracle import modal
+from oracle import parareal as opr
+from paper_1409_8563_gb300 import configs, inputs, native
+from tests.helpers import TOL, oracle_F, oracle_G, rel_inf, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F32, F64 = native.F32, native.F64
+
+
+def dev(x, dtype):
+    t = torch.float64 if dtype == F64 else torch.float32
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda", t)
+
+
+def host(t):
+    return t.double().cpu().numpy()
+
+
+def small_cfg(n, n_slices, dtype, a=(1.0, 1.0, 1.0), omega=100.0):
+    # the paper's parameters with fewer points and steps: T = 0.1, nu0 = 0.1
+    return configs.paper_faithful(n=n, n_slices=n_slices, omega=omega, fine_log2=10,
+                                  coarse_log2=7, dtype=dtype, a=a)[0]
+
+
+@pytest.mark.parametrize("n,dtype", [(16, F64), (24, F64), (32, F32)])
+def test_c4_fine_propagator_matches_oracle(n, dtype):
+    cfg = small_cfg(n, 4, dtype)
+    ctx = native.Parareal(cfg)
+    assert ctx.launch_shape()[0][0] == 1        # the per-stage kernels
+    src = np.stack([inputs.spectral_ic(n, seed=30 + s, kmax=n // 4) for s in range(3)])
+    dsrc = dev(src, dtype)
+    ddst = torch.empty_like(dsrc)
+    ctx.propagate(0, dsrc, ddst, 1, 3)           # slices 1, 2, 3
+    got = host(ddst)
+    F = oracle_F(cfg)
+    for s in range(3):
+        ref = F(src[s], 1 + s)
+        assert rel_l2(got[s], ref) < TOL[dtype], (s, rel_l2(got[s], ref))
+    ctx.close()
+
+
+@pytest.mark.parametrize("dtype,a", [(F64, (1.0, 1.0, 1.0)), (F64, (1.0, -0.5, 0.25)),
+                                     (F32, (-1.0, 0.5, -0.25))])
+def test_euler_upwind_coarse_propagator_matches_oracle(dtype, a):
+    """Both upwind branches (a > 0 and a < 0) against Algorithm 2 in the oracle."""
+    n = 16
+    cfg = small_cfg(n, 4, dtype, a=a)
+    ctx = native.Parareal(cfg)
+    src = np.stack([inputs.spectral_ic(n, seed=40 + s, kmax=n // 4) for s in range(2)])
+    dsrc = dev(src, dtype)
+    ddst = torch.empty_like(dsrc)
+    ctx.propagate(1, dsrc, ddst, 2, 2)           # slices 2, 3
+    got = host(ddst)
+    G = oracle_G(cfg)
+    for s in range(2):
+        ref = G(src[s], 2 + s)
+        assert rel_l2(got[s], ref) < TOL[dtype], (s, rel_l2(got[s], ref))
+    ctx.close()
+
+
+def read_all(ctx, cfg):
+    buf = torch.empty((cfg.n,) * 3, dtype=torch.float64, device="cuda")
+    out = []
+    for s in range(cfg.n_slices + 1):
+        ctx.get_slice(s, buf)
+        out.append(host(buf))
+    return out
+
+
+def test_paper_scheme_parareal_matches_oracle():
+    n, N, K = 16, 4, 2
+    cfg = small_cfg(n, N, F64)
+    u0 = inputs.spectral_ic(n, seed=3, kmax=4)
+    ctx = native.Parareal(cfg)
+    ctx.set_problem(dev(u0, F64))
+    ctx.iterate(K, 0.0, native.STOP_NONE)
+    got = read_all(ctx, cfg)
+    hist = opr.parareal(oracle_F(cfg), oracle_G(cfg), u0, N, K)
+    for s in range(1, N + 1):
+        assert rel_l2(got[s], hist[K][s]) < 1e-12, (s, rel_l2(got[s], hist[K][s]))
+    # k = N reproduces the serial fine run exactly (Eq. parareal, R3 order)
+    ctx.set_problem(dev(u0, F64))
+    ctx.iterate(N, 0.0, native.STOP_NONE)
+    last = read_all(ctx, cfg)[N]
+    ref = torch.empty((n,) * 3, dtype=torch.float64, device="cuda")
+    ctx.serial_fine(ref, as_reference=False)
+    assert np.array_equal(last, host(ref))
+    ctx.close()
+
+
+def _paper_run(omega, n_slices):
+    cfg, u0 = configs.paper_faithful(n=128, n_slices=n_slices, omega=omega)
+    ctx = native.Parareal(cfg)
+    ctx.set_problem(dev(u0, F64))
+    exact = modal.analytic_paper_field(128, cfg.T, cfg.nu0, cfg.nu_amp, cfg.nu_omega)
+    return cfg, ctx, exact
+
+
+@pytest.mark.parametrize("omega", [0.0, 100.0])
+def test_paper_coarse_error_at_full_size(omega):
+    """Sec. 3.1: eps_coarse ~ 4.5e-2 for both omega (forward Euler, upwind, T/2^11)."""
+    cfg, ctx, exact = _paper_run(omega, 8)
+    ctx.coarse_sweep(0, cfg.n_slices, chain=True)
+    u = torch.empty((128,) * 3, dtype=torch.float64, device="cuda")
+    ctx.get_slice(cfg.n_slices, u)
+    e = rel_inf(host(u), exact)
+    assert 4.45e-2 <= e < 4.55e-2, e
+    ctx.close()
+
+
+@pytest.mark.parametrize("omega,eps_lo,eps_hi,d3_lo,d3_hi", [
+    (0.0, 1.85e-7, 1.95e-7, 1.9e-8, 1.9e-6),
+    (100.0, 4.75e-6, 4.85e-6, 0.0, 4.8e-7)])
+def test_paper_fine_error_and_three_iterations_at_full_size(omega, eps_lo, eps_hi, d3_lo, d3_hi):
+    """Sec. 3.1: eps_fine ~ 1.9e-7 (omega = 0) and 4.8e-6 (omega = 100, nu frozen);
+    Sec. 3.4.1: after three iterations with N_p = 8 the defect against the
+    serial fine run is far below eps_fine for omega = 100 and of the order of
+    the fine error for omega = 0."""
+    cfg, ctx, exact = _paper_run(omega, 8)
+    u = torch.empty((128,) * 3, dtype=torch.float64, device="cuda")
+    ctx.serial_fine(u, as_reference=True)
+    e = rel_inf(host(u), exact)
+    assert eps_lo <= e < eps_hi, e
+    k, h = ctx.iterate(3, 0.0, native.STOP_NONE)
+    d3 = h[2, 2]
+    assert d3_lo < d3 < d3_hi, h[:, 2]
+    ctx.close()
