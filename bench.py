@@ -424,9 +424,11 @@ def run_paper_faithful(args):
 
 
 def run_learned_128(args):
-    """128^3, N = 32: learned coarse propagator (trained here on pairs the
-    fine solver generates) vs stencil coarse propagator vs shift only vs
-    serial fine: iterations and time to d^k <= 1e-6."""
+    """128^3, N = 32: learned coarse propagators (trained here on pairs the
+    fine solver generates) vs the stencil coarse propagator vs shift only vs
+    serial fine: iterations and time to d^k <= 1e-6.  Two nets correct the
+    stencil propagator: the GELU network as specified, and the linear one
+    (nu as a factor) with the correction applied to U^{k+1}[n] - U^k[n]."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -434,12 +436,17 @@ def run_learned_128(args):
     from paper_1409_8563_gb300 import configs, inputs, native
     base, u0 = configs.fp32_128()
     n, N = base.n, base.n_slices
-    mk = lambda kind, r, dtg, skip=native.SKIP_SHIFT: native.Config.make(
-        n, N, base.T, base.dt_fine, dtg, r, fine_dtype=native.F32, coarse_kind=kind,
-        nu0=base.nu0, nu_amp=base.nu_amp, nu_omega=base.nu_omega, learned_skip=skip)
-    # the net corrects the stencil propagator (RK4 on 32^3 at 1/256)
+    mk = lambda kind, r, dtg, skip=native.SKIP_SHIFT, act=native.ACT_GELU, \
+        form=native.CORRECTION_STANDARD: native.Config.make(
+            n, N, base.T, base.dt_fine, dtg, r, fine_dtype=native.F32, coarse_kind=kind,
+            nu0=base.nu0, nu_amp=base.nu_amp, nu_omega=base.nu_omega, learned_skip=skip,
+            learned_act=act, correction_form=form)
+    # the nets correct the stencil propagator (RK4 on 32^3 at 1/256)
     learned = native.Parareal(mk(native.COARSE_LEARNED, base.coarse_factor, base.dt_coarse,
                                  native.SKIP_STENCIL))
+    linear = native.Parareal(mk(native.COARSE_LEARNED, base.coarse_factor, base.dt_coarse,
+                                native.SKIP_STENCIL, native.ACT_LINEAR,
+                                native.CORRECTION_DIFFERENCE))
     n_ics = args.n_ics
     t0 = time.perf_counter()
     # k^-2 fields to k = 32 plus white noise: broadband inputs, so the net sees
@@ -453,17 +460,24 @@ def run_learned_128(args):
     torch.cuda.synchronize()
     pairs_s = time.perf_counter() - t0
     del ics
-    learned.set_coarse_model(inputs.initial_weights(seed=0))
-    t0 = time.perf_counter()
-    hist = learned.train_coarse(pu, pf, sl, epochs=args.epochs, batch=args.batch, lr=args.lr, seed=1)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
+    train = {}
+    for name, c in (("learned_gelu", learned), ("learned_linear", linear)):
+        c.set_coarse_model(inputs.initial_weights(seed=0))
+        t0 = time.perf_counter()
+        hist = c.train_coarse(pu, pf, sl, epochs=args.epochs, batch=args.batch, lr=args.lr, seed=1)
+        torch.cuda.synchronize()
+        train[name] = {"loss_first_last": [float(hist[0]), float(hist[-1])],
+                       "train_s": time.perf_counter() - t0}
     del pu, pf
     torch.cuda.empty_cache()
     u = torch.from_numpy(u0).cuda()
     res = {}
-    ctxs = {"learned": learned,
+    ctxs = {"learned_linear": linear,
+            "learned_gelu": learned,
             "stencil": native.Parareal(base),
+            "stencil_difference_form": native.Parareal(
+                mk(native.COARSE_STENCIL, base.coarse_factor, base.dt_coarse,
+                   form=native.CORRECTION_DIFFERENCE)),
             "shift": native.Parareal(mk(native.COARSE_SHIFT, 1, base.T / N))}
     serial_ms = None
     for name, c in ctxs.items():
@@ -480,8 +494,7 @@ def run_learned_128(args):
         res[name] = {"k_star": k, "time_to_1e-6_ms": ms, "defects": [float(x) for x in h[:, 2]]}
     print(json.dumps({"workload": "learned_128", "serial_fine_ms": serial_ms, "runs": res,
                       "train": {"pairs": int(len(sl)), "epochs": args.epochs, "batch": args.batch,
-                                "lr": args.lr, "loss": [float(x) for x in hist],
-                                "pairs_s": pairs_s, "train_s": train_s}}))
+                                "lr": args.lr, "pairs_s": pairs_s, **train}}))
     for c in ctxs.values():
         c.close()
     return 0

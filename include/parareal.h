@@ -116,7 +116,27 @@ typedef struct {
     int allow_unstable;    /* nonzero: stability pre-check failures become a warning */
     int learned_skip;      /* PARAREAL_SKIP_*: the skip path of the learned propagator */
     int fine_scheme;       /* PARAREAL_SCHEME_*: spatial operator of F */
+    int learned_act;       /* PARAREAL_ACT_*: the learned propagator's layers */
+    int correction_form;   /* PARAREAL_CORRECTION_*: how Eq. (parareal) is evaluated */
 } parareal_config;
+
+/* Layers of the learned coarse propagator (coarse_kind LEARNED / SHIFT):
+ * GELU   the network as specified: GELU after the first three convolutions,
+ *        biases, second input channel the constant nu(t_n)/nu0;
+ * LINEAR identity activations, no biases, second input channel
+ *        nu(t_n)/nu0 * Sk(u) (Sk the skip propagator): G is then linear in u,
+ *        with a kernel that depends on nu(t_n). */
+enum { PARAREAL_ACT_GELU = 0, PARAREAL_ACT_LINEAR = 1 };
+
+/* Evaluation of the correction (Eq. parareal):
+ * STANDARD   U^{k+1}[n+1] = F(U^k[n]) + (G(U^{k+1}[n]) - G(U^k[n])), as printed;
+ * DIFFERENCE U^{k+1}[n+1] = F(U^k[n]) + G(U^{k+1}[n] - U^k[n]), the same for a
+ *            linear G (stencil, Euler/upwind, shift, or the LINEAR learned
+ *            propagator; rejected for a GELU network).  Rounding in G then
+ *            scales with the change of its input instead of with the field,
+ *            so a G evaluated in low precision (BF16) does not put a floor
+ *            under the defect.  No counterpart in the paper. */
+enum { PARAREAL_CORRECTION_STANDARD = 0, PARAREAL_CORRECTION_DIFFERENCE = 1 };
 
 /* Skip path of the learned coarse propagator (coarse_kind LEARNED / SHIFT):
  * SHIFT   G = S(u) + Net([S(u), nu/nu0]) on the grid n / coarse_factor;

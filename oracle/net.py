@@ -11,6 +11,10 @@ channels, with GELU after the first three.  Loss: mean squared error against
 F(u) over all points of all samples.  Adam (Kingma & Ba, 2015) with bias
 correction updates FP32 master weights.
 
+Linear mode (``linear=True``): identity activations, biases ignored, and the
+second input channel nu_hat * S(u) instead of the constant nu_hat, so that
+G(u) is linear in u with a kernel that depends on nu(t_n).
+
 BF16 emulation.  With ``bf16=True`` the values the CUDA path stores in
 bfloat16 are rounded to bfloat16 (round to nearest even) at the same points:
 weights, the network input, the three activations, and the gradients of the
@@ -49,32 +53,36 @@ def init_params(seed=0, scale=None):
     return params
 
 
-def forward(u, nu_hat, params, shift, bf16_emul=False):
+def forward(u, nu_hat, params, shift, bf16_emul=False, linear=False):
     """Return (G(u), cache).  u: [n][n][n] FP64."""
     q = bf16 if bf16_emul else (lambda v: np.asarray(v, dtype=np.float64))
     su = core.shift(u, shift)
-    x = np.stack([q(su), q(np.full(su.shape, nu_hat))])
+    if linear:
+        x = np.stack([q(su), q(np.float64(nu_hat)) * q(su)])
+    else:
+        x = np.stack([q(su), q(np.full(su.shape, nu_hat))])
     cache = {"x": [x], "z": [], "su": su}
     h = x
     for li, (W, b) in enumerate(params):
-        z = core.conv3d_fwd(h, q(W), b)
+        z = core.conv3d_fwd(h, q(W), np.zeros_like(b) if linear else b)
         cache["z"].append(z)
         if li < len(params) - 1:
-            h = q(core.gelu(z))
+            h = q(z if linear else core.gelu(z))
             cache["x"].append(h)
         else:
             h = z
     return su + h[0], cache
 
 
-def loss_and_grads(u_list, nu_list, target_list, params, shift, bf16_emul=False):
-    """MSE over all points of all samples and its gradients (FP64)."""
+def loss_and_grads(u_list, nu_list, target_list, params, shift, bf16_emul=False, linear=False):
+    """MSE over all points of all samples and its gradients (FP64).  In linear
+    mode the bias gradients are zero (the biases are not used)."""
     q = bf16 if bf16_emul else (lambda v: np.asarray(v, dtype=np.float64))
     count = sum(u.size for u in u_list)
     grads = [[np.zeros_like(W), np.zeros_like(b)] for W, b in params]
     loss = 0.0
     for u, nu_hat, tgt in zip(u_list, nu_list, target_list):
-        out, c = forward(u, nu_hat, params, shift, bf16_emul)
+        out, c = forward(u, nu_hat, params, shift, bf16_emul, linear)
         r = out - tgt
         loss += float(np.sum(r * r))
         dz = q((2.0 / count) * r)[None]
@@ -83,11 +91,12 @@ def loss_and_grads(u_list, nu_list, target_list, params, shift, bf16_emul=False)
             x = c["x"][li]
             dW, db = core.conv3d_wgrad(x, dz)
             grads[li][0] += dW
-            grads[li][1] += db
+            if not linear:
+                grads[li][1] += db
             if li == 0:
                 break
             da = core.conv3d_dgrad(dz, q(W))
-            dz = q(da * core.gelu_grad(c["z"][li - 1]))
+            dz = q(da if linear else da * core.gelu_grad(c["z"][li - 1]))
     return loss / count, grads
 
 

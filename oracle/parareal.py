@@ -27,10 +27,13 @@ def serial_fine(F, u0, n_slices):
     return out
 
 
-def parareal(F, G, u0, n_slices, k_max):
+def parareal(F, G, u0, n_slices, k_max, form="standard"):
     """Return [U^0, U^1, ..., U^{k_max}], each a list of N_p + 1 fields.
 
-    U^k[n] approximates u(t_n) after k Parareal iterations.
+    U^k[n] approximates u(t_n) after k Parareal iterations.  form="standard"
+    evaluates Eq. (parareal) as printed, F(U^k[n]) + (G(U^{k+1}[n]) - G(U^k[n]));
+    form="difference" evaluates F(U^k[n]) + G(U^{k+1}[n] - U^k[n]), the same
+    for a linear G.
     """
     u0 = np.array(u0, dtype=np.float64)
     # Initial guess: one serial run of the coarse propagator.
@@ -45,9 +48,12 @@ def parareal(F, G, u0, n_slices, k_max):
         # Coarse propagator and correction, slice after slice (serial part).
         U_new = [u0]
         for n in range(n_slices):
-            g = G(U_new[n], n)
-            U_new.append(F_val[n + 1] + (g - G_old[n + 1]))
-            G_old[n + 1] = g
+            if form == "difference":
+                U_new.append(F_val[n + 1] + G(U_new[n] - U[n], n))
+            else:
+                g = G(U_new[n], n)
+                U_new.append(F_val[n + 1] + (g - G_old[n + 1]))
+                G_old[n + 1] = g
         U = U_new
         history.append(list(U))
     return history

@@ -114,6 +114,13 @@ static parareal_status validate(const parareal_config *cfg, long long *Nf, long 
     if (cfg->coarse_kind < PARAREAL_COARSE_STENCIL || cfg->coarse_kind > PARAREAL_COARSE_EULER_UPWIND) { *msg = "coarse_kind"; return PARAREAL_E_INVALID; }
     if (cfg->coarse_kind == PARAREAL_COARSE_EULER_UPWIND && cfg->coarse_factor != 1) { *msg = "the Euler/upwind coarse propagator runs on the fine grid (coarse_factor 1)"; return PARAREAL_E_INVALID; }
     if (cfg->fine_scheme != PARAREAL_SCHEME_C2 && cfg->fine_scheme != PARAREAL_SCHEME_C4) { *msg = "fine_scheme"; return PARAREAL_E_INVALID; }
+    if (cfg->learned_act != PARAREAL_ACT_GELU && cfg->learned_act != PARAREAL_ACT_LINEAR) { *msg = "learned_act"; return PARAREAL_E_INVALID; }
+    if (cfg->correction_form != PARAREAL_CORRECTION_STANDARD && cfg->correction_form != PARAREAL_CORRECTION_DIFFERENCE) { *msg = "correction_form"; return PARAREAL_E_INVALID; }
+    if (cfg->correction_form == PARAREAL_CORRECTION_DIFFERENCE && cfg->coarse_kind == PARAREAL_COARSE_LEARNED &&
+        cfg->learned_act != PARAREAL_ACT_LINEAR) {
+        *msg = "the difference form of the correction needs a linear coarse propagator";
+        return PARAREAL_E_INVALID;
+    }
     if (cfg->learned_skip != PARAREAL_SKIP_SHIFT && cfg->learned_skip != PARAREAL_SKIP_STENCIL) { *msg = "learned_skip"; return PARAREAL_E_INVALID; }
     const double slice = cfg->T / cfg->n_slices;
     if (!is_integer_ratio(slice, cfg->dt_fine, Nf)) { *msg = "T/(n_slices dt_fine) must be an integer"; return PARAREAL_E_INVALID; }
@@ -412,17 +419,17 @@ static parareal_status coarse_apply_t(parareal_ctx *c, const double *Uin, int s,
 // Fv / gold may be null (read as zero).
 template <typename T>
 static parareal_status correct_t(parareal_ctx *c, int s, const void *gnew, const void *gold,
-                                 bool with_fine)
+                                 bool with_fine, double *dU = nullptr)
 {
     const T *Fv = with_fine ? static_cast<const T *>(c->Fv) + (long long)(s + 1) * c->P : nullptr;
     double *U = c->U + (long long)(s + 1) * c->P;
     if (!c->g_fine) {
         LK((launch_correct<T, T>(Fv, static_cast<const T *>(gnew), static_cast<const T *>(gold), U,
-                                 c->n, c->r, c->partials, c->nblk, c->st)));
+                                 c->n, c->r, c->partials, c->nblk, c->st, dU)));
     } else {
         LK((launch_correct<T, double>(Fv, static_cast<const double *>(gnew),
                                       static_cast<const double *>(gold), U, c->n, 1, c->partials,
-                                      c->nblk, c->st)));
+                                      c->nblk, c->st, dU)));
     }
     LK(launch_reduce_partials(c->partials, c->nblk, c->slice_norms + 5ll * (s + 1), c->st));
     return PARAREAL_OK;
@@ -455,15 +462,30 @@ parareal_status iter_enqueue(parareal_ctx *c)
     const int K = c->k_total;
     parareal_status s = DISPATCH(c, fine_sweep_t, K, c->N - K);
     if (s != PARAREAL_OK) return s;
-    // slice K+1: its input U[K] did not change, so G's difference is zero
-    s = DISPATCH(c, correct_t, K, c->gold[K + 1], c->gold[K + 1], true);
-    if (s != PARAREAL_OK) return s;
-    for (int n = K + 1; n < c->N; ++n) {
-        s = DISPATCH(c, coarse_apply_t, c->U + (long long)n * c->P, n, c->gspare);
+    if (c->cfg.correction_form == PARAREAL_CORRECTION_DIFFERENCE) {
+        // U[n+1] = Fv[n+1] + G(D_n), D_n = U^{k+1}[n] - U^k[n] (G linear); the
+        // correction of slice n writes D_{n+1}.  D_K = 0: slice K+1 takes Fv alone.
+        double *Din = c->dA, *Dout = c->dB;
+        s = DISPATCH(c, correct_t, K, c->gold[K + 1], c->gold[K + 1], true, Din);
         if (s != PARAREAL_OK) return s;
-        s = DISPATCH(c, correct_t, n, c->gspare, c->gold[n + 1], true);
+        for (int n = K + 1; n < c->N; ++n) {
+            s = DISPATCH(c, coarse_apply_t, Din, n, c->gspare);
+            if (s != PARAREAL_OK) return s;
+            s = DISPATCH(c, correct_t, n, c->gspare, nullptr, true, Dout);
+            if (s != PARAREAL_OK) return s;
+            std::swap(Din, Dout);
+        }
+    } else {
+        // slice K+1: its input U[K] did not change, so G's difference is zero
+        s = DISPATCH(c, correct_t, K, c->gold[K + 1], c->gold[K + 1], true);
         if (s != PARAREAL_OK) return s;
-        std::swap(c->gspare, c->gold[n + 1]);
+        for (int n = K + 1; n < c->N; ++n) {
+            s = DISPATCH(c, coarse_apply_t, c->U + (long long)n * c->P, n, c->gspare);
+            if (s != PARAREAL_OK) return s;
+            s = DISPATCH(c, correct_t, n, c->gspare, c->gold[n + 1], true);
+            if (s != PARAREAL_OK) return s;
+            std::swap(c->gspare, c->gold[n + 1]);
+        }
     }
     if (c->has_ref) {
         LK(launch_diff_norms<double>(c->U + (long long)c->N * c->P, c->ref, c->P, c->partials, c->nblk, c->st));
@@ -594,6 +616,8 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
     const size_t cbytes = (c->r > 1 ? Pc : P) * e;
     ok = ok && alloc(&c->cA, cbytes) && alloc(&c->cB, cbytes) && alloc(&c->cC, cbytes) && alloc(&c->cD, cbytes);
     ok = ok && alloc((void **)&c->tmpd, 2 * P * sizeof(double));
+    if (cfg->correction_form == PARAREAL_CORRECTION_DIFFERENCE)
+        ok = ok && alloc((void **)&c->dA, P * sizeof(double)) && alloc((void **)&c->dB, P * sizeof(double));
     ok = ok && alloc(&c->wS, P * e);
     c->nblk = correct_blocks(c->P);
     ok = ok && alloc((void **)&c->partials, 5 * sizeof(double) * (size_t)c->nblk);
@@ -625,7 +649,7 @@ extern "C" void parareal_destroy(parareal_ctx *c)
     if (!c) return;
     cudaStreamSynchronize(c->st);
     void *ptrs[] = {c->U, c->Fv, c->gspare, c->wA, c->wB, c->wC, c->cA, c->cB, c->cC, c->cD,
-                    c->tmpd, c->wS, c->ref, c->partials, c->slice_norms};
+                    c->tmpd, c->wS, c->ref, c->partials, c->slice_norms, c->dA, c->dB};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (void *p : c->gold)

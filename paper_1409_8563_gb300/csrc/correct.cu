@@ -96,7 +96,8 @@ __device__ __forceinline__ void lin_weights(int i, int r, int nc, int &lo, int &
 template <typename TF, typename TG>
 __global__ void __launch_bounds__(RED_THREADS)
 correct_kernel(const TF *__restrict__ Fv, const TG *__restrict__ gnew, const TG *__restrict__ gold,
-               double *__restrict__ U, int n, int r, double *__restrict__ partials)
+               double *__restrict__ U, int n, int r, double *__restrict__ partials,
+               double *__restrict__ dU)
 {
     Partial acc{0ull, 0ull, 0.0, 0.0, 0};
     const int nc = n / r;
@@ -143,6 +144,7 @@ correct_kernel(const TF *__restrict__ Fv, const TG *__restrict__ gnew, const TG 
             const double un = (Fv ? (double)Fv[p] : 0.0) + dg;
             const double du = un - U[p];
             U[p] = un;
+            if (dU) dU[p] = du;
             const unsigned long long bu = abs_bits(un), bd = abs_bits(du);
             acc.bad |= nonfinite_bits(bu) ? 1 : 0;
             acc.mx_u = bu > acc.mx_u ? bu : acc.mx_u;
@@ -164,20 +166,23 @@ int correct_blocks(long long P)
 
 template <typename TF, typename TG>
 cudaError_t launch_correct(const TF *Fv, const TG *gnew, const TG *gold, double *U, int n, int r,
-                           double *partials, int nblocks, cudaStream_t st)
+                           double *partials, int nblocks, cudaStream_t st, double *dU)
 {
-    correct_kernel<TF, TG><<<nblocks, RED_THREADS, 0, st>>>(Fv, gnew, gold, U, n, r, partials);
+    correct_kernel<TF, TG><<<nblocks, RED_THREADS, 0, st>>>(Fv, gnew, gold, U, n, r, partials, dU);
     return cudaGetLastError();
 }
 template cudaError_t launch_correct<float, float>(const float *, const float *, const float *,
-                                                  double *, int, int, double *, int, cudaStream_t);
+                                                  double *, int, int, double *, int, cudaStream_t,
+                                                  double *);
 template cudaError_t launch_correct<float, double>(const float *, const double *, const double *,
-                                                   double *, int, int, double *, int, cudaStream_t);
+                                                   double *, int, int, double *, int, cudaStream_t,
+                                                  double *);
 template cudaError_t launch_correct<double, double>(const double *, const double *,
                                                     const double *, double *, int, int, double *,
-                                                    int, cudaStream_t);
+                                                    int, cudaStream_t, double *);
 template cudaError_t launch_correct<double, float>(const double *, const float *, const float *,
-                                                   double *, int, int, double *, int, cudaStream_t);
+                                                   double *, int, int, double *, int, cudaStream_t,
+                                                  double *);
 
 // max|a - b| and max|b| (the defect d^k of Eq. defect), same partial layout.
 template <typename TA>

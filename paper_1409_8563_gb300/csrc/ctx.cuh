@@ -32,6 +32,7 @@ struct NetState {
     float *h_nub = nullptr;                   // pinned staging for nu of a batch
     double *h_loss = nullptr;
     int adam_t = 0;
+    int lin = 0;               // linear mode (PARAREAL_ACT_LINEAR)
     bool has_model = false;
 };
 
@@ -52,6 +53,7 @@ struct parareal_ctx {
     void *wA = nullptr, *wB = nullptr, *wC = nullptr;
     void *cA = nullptr, *cB = nullptr, *cC = nullptr, *cD = nullptr;
     double *tmpd = nullptr;       // 2P doubles: conversions and propagate() scratch
+    double *dA = nullptr, *dB = nullptr;   // U^{k+1}[n] - U^k[n] (difference-form correction)
     void *wS = nullptr;           // P of T: state of the serial fine run
     double *ref = nullptr;
     double *partials = nullptr;

@@ -117,10 +117,11 @@ cudaError_t launch_restrict(const double *fine, int n, int r, T *coarse, cudaStr
 // Correction of Eq. (parareal) for one slice, with per-block norm partials:
 //   U[p] <- Fv[p] + (g_new[p] - g_old[p]),  g = trilinear prolongation of the
 //   coarse T fields cnew/cold by factor r (r == 1: plain FP64 fields gnew/gold).
-// Partials per block: {max|dU|, max|U|, sum dU^2, sum U^2, nan}.
+// Partials per block: {max|dU|, max|U|, sum dU^2, sum U^2, nan}.  A non-null
+// dU receives the change U_new - U_old of every point.
 template <typename TF, typename TG>
 cudaError_t launch_correct(const TF *Fv, const TG *gnew, const TG *gold, double *U, int n, int r,
-                           double *partials, int nblocks, cudaStream_t st);
+                           double *partials, int nblocks, cudaStream_t st, double *dU = nullptr);
 int correct_blocks(long long P);
 
 // Max-abs of (a - b) and of b over one field (defect d^k), per-block partials.

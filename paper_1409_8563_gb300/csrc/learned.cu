@@ -43,6 +43,7 @@ parareal_status net_setup(parareal_ctx *c)
     // fine grid (no shift: the stencil propagator already transports)
     const bool stencil_skip = c->cfg.learned_skip == PARAREAL_SKIP_STENCIL;
     S.m = stencil_skip ? c->n : c->n / c->r;
+    S.lin = c->cfg.learned_act == PARAREAL_ACT_LINEAR;
     if (S.m % 8) return fail(c, PARAREAL_E_INVALID, "the learned propagator needs a grid edge that is a multiple of 8");
     S.Pm = (long long)S.m * S.m * S.m;
     const double slice = c->cfg.T / c->N;
@@ -90,11 +91,12 @@ parareal_status net_apply(parareal_ctx *c, const TU *u, int slice, TG *out)
 {
     NetState &S = c->net;
     const float *b = S.master;
-    LK(launch_net_in_fwd<TU>(u, S.m, S.shift, S.nu_slices + slice, 1, S.W1q, b + NET_B1, nullptr, S.ia, c->st));
-    LK(launch_net_mid(0, S.ia, S.m, 1, S.B2f, b + NET_B2, nullptr, nullptr, S.ib, c->st));
-    LK(launch_net_mid(0, S.ib, S.m, 1, S.B3f, b + NET_B3, nullptr, nullptr, S.ia, c->st));
+    LK(launch_net_in_fwd<TU>(u, S.m, S.shift, S.nu_slices + slice, 1, S.W1q, b + NET_B1, nullptr, S.ia, c->st,
+                             S.lin));
+    LK(launch_net_mid(0, S.ia, S.m, 1, S.B2f, b + NET_B2, nullptr, nullptr, S.ib, c->st, S.lin));
+    LK(launch_net_mid(0, S.ib, S.m, 1, S.B3f, b + NET_B3, nullptr, nullptr, S.ia, c->st, S.lin));
     LK((launch_net_out_fwd<TU, TG>(S.ia, S.m, 1, S.W4q, b + NET_B4, u, S.shift, out, nullptr, 0.f,
-                                   nullptr, nullptr, c->st)));
+                                   nullptr, nullptr, c->st, S.lin)));
     return PARAREAL_OK;
 }
 template parareal_status net_apply<double, double>(parareal_ctx *, const double *, int, double *);
@@ -144,26 +146,34 @@ static parareal_status net_loss_grad(parareal_ctx *c, int batch, double *loss_sl
     const long long F = (long long)batch * S.Pm;
     const int tiles = (int)((long long)batch * (m / 8) * (m / 8) * (m / 8));
     // forward, keeping pre-activations
-    LK(launch_net_in_fwd<float>(S.ub, m, S.shift, S.nub, batch, S.W1q, b + NET_B1, S.z1, S.a1, c->st));
-    LK(launch_net_mid(0, S.a1, m, batch, S.B2f, b + NET_B2, nullptr, S.z2, S.a2, c->st));
-    LK(launch_net_mid(0, S.a2, m, batch, S.B3f, b + NET_B3, nullptr, S.z3, S.a3, c->st));
+    LK(launch_net_in_fwd<float>(S.ub, m, S.shift, S.nub, batch, S.W1q, b + NET_B1, S.z1, S.a1, c->st,
+                                S.lin));
+    LK(launch_net_mid(0, S.a1, m, batch, S.B2f, b + NET_B2, nullptr, S.z2, S.a2, c->st, S.lin));
+    LK(launch_net_mid(0, S.a2, m, batch, S.B3f, b + NET_B3, nullptr, S.z3, S.a3, c->st, S.lin));
     const float gscale = (float)(2.0 / (double)F);
     LK((launch_net_out_fwd<float, float>(S.a3, m, batch, S.W4q, b + NET_B4, S.ub, S.shift, nullptr,
-                                         S.fb, gscale, S.dz4, S.loss_parts, c->st)));
+                                         S.fb, gscale, S.dz4, S.loss_parts, c->st, S.lin)));
     LK(launch_reduce_loss(S.loss_parts, tiles, loss_slot, c->st));
     // backward
     const int nb = net_partial_blocks(m, batch);
     LK(launch_net_out_wgrad(S.a3, S.dz4, m, batch, S.partials, nb, c->st));
     LK(launch_reduce_cols(S.partials, nb, NET_OUT_PARTIAL, NET_OUT_PARTIAL, S.grad + NET_W4, c->st));
-    LK(launch_net_out_dgrad(S.dz4, m, batch, S.W4q, S.z3, S.dzA, c->st));          // dz3
+    LK(launch_net_out_dgrad(S.dz4, m, batch, S.W4q, S.z3, S.dzA, c->st, S.lin));   // dz3
     LK(launch_net_mid_wgrad(S.a2, S.dzA, m, batch, S.partials, nb, c->st));
     LK(launch_reduce_mid(S.partials, nb, S.grad + NET_W3, S.grad + NET_B3, c->st));
-    LK(launch_net_mid(1, S.dzA, m, batch, S.B3b, nullptr, S.z2, nullptr, S.dzB, c->st));  // dz2
+    LK(launch_net_mid(1, S.dzA, m, batch, S.B3b, nullptr, S.z2, nullptr, S.dzB, c->st, S.lin));  // dz2
     LK(launch_net_mid_wgrad(S.a1, S.dzB, m, batch, S.partials, nb, c->st));
     LK(launch_reduce_mid(S.partials, nb, S.grad + NET_W2, S.grad + NET_B2, c->st));
-    LK(launch_net_mid(1, S.dzB, m, batch, S.B2b, nullptr, S.z1, nullptr, S.dzA, c->st));  // dz1
-    LK(launch_net_in_wgrad<float>(S.ub, m, batch, S.shift, S.nub, S.dzA, S.partials, nb, c->st));
+    LK(launch_net_mid(1, S.dzB, m, batch, S.B2b, nullptr, S.z1, nullptr, S.dzA, c->st, S.lin));  // dz1
+    LK(launch_net_in_wgrad<float>(S.ub, m, batch, S.shift, S.nub, S.dzA, S.partials, nb, c->st, S.lin));
     LK(launch_reduce_cols(S.partials, nb, NET_IN_PARTIAL, NET_IN_PARTIAL, S.grad + NET_W1, c->st));
+    if (S.lin) {
+        // the linear net has no biases: their gradients are zero and Adam leaves them
+        CK(cudaMemsetAsync(S.grad + NET_B1, 0, 16 * 4, c->st));
+        CK(cudaMemsetAsync(S.grad + NET_B2, 0, 16 * 4, c->st));
+        CK(cudaMemsetAsync(S.grad + NET_B3, 0, 16 * 4, c->st));
+        CK(cudaMemsetAsync(S.grad + NET_B4, 0, 4, c->st));
+    }
     return PARAREAL_OK;
 }
 

@@ -3,8 +3,11 @@
 //   G(u, t_n) = S(u) + Net([S(u), nu(t_n)/nu0]),
 //   Net = conv3(2->16) GELU conv3(16->16) GELU conv3(16->16) GELU conv3(16->1)
 //
-// with S the periodic integer shift and conv3 a periodic 3x3x3
-// cross-correlation.  Storage: activations channels-last in BF16
+// with S the skip propagator (periodic integer shift, or the stencil
+// propagator) and conv3 a periodic 3x3x3 cross-correlation.  Linear mode
+// (lin != 0): identity activations, no biases, and the second input channel
+// nu_hat * S(u) instead of the constant nu_hat, so that G is linear in u with
+// a kernel that depends on nu(t_n).  Storage: activations channels-last in BF16
 // ([point][16], 32 bytes per point), pre-activations in FP32, weights as FP32
 // masters with BF16 operand copies; all accumulation in FP32.
 //
@@ -100,11 +103,13 @@ __device__ __forceinline__ void load_halo16(uint4 *sm, const bf16 *__restrict__ 
 // ---------------------------------------------------------------- layer 1
 
 // z1 = conv(x0, W1) + b1, a1 = bf16(gelu(z1)), x0 = [bf16(S(u)), bf16(nu_hat)].
+// Linear mode: x0 = [bf16(S(u)), bf16(nu_hat) bf16(S(u))], no bias, a1 = bf16(z1);
+// the two channels share their input, so their weights are combined per sample.
 template <typename TU>
 __global__ void __launch_bounds__(512)
 net_in_fwd(const TU *__restrict__ u, int m, int sx, int sy, int sz, const float *__restrict__ nu_hat,
            const float *__restrict__ W1q, const float *__restrict__ b1, float *__restrict__ z1,
-           bf16 *__restrict__ a1)
+           bf16 *__restrict__ a1, int lin)
 {
     __shared__ float xs[1000];
     __shared__ float w[16 * 27];
@@ -120,12 +125,15 @@ net_in_fwd(const TU *__restrict__ u, int m, int sx, int sy, int sz, const float 
         const int gz = wrap(wrap(T.oz + hz - 1, m) - sz + m, m);
         xs[i] = bf16r((float)us[((long long)gz * m + gy) * m + gx]);
     }
-    for (int i = threadIdx.x; i < 16 * 27; i += blockDim.x)
-        w[i] = W1q[(i / 27) * 54 + (i % 27)];
+    const float nq = bf16r(nu_hat[s]);
+    for (int i = threadIdx.x; i < 16 * 27; i += blockDim.x) {
+        const int c = i / 27, t = i % 27;
+        w[i] = lin ? fmaf(nq, W1q[c * 54 + 27 + t], W1q[c * 54 + t]) : W1q[c * 54 + t];
+    }
     if (threadIdx.x < 16) {
-        const float nq = bf16r(nu_hat[s]);
-        float acc = b1[threadIdx.x];
-        for (int t = 0; t < 27; ++t) acc = fmaf(W1q[threadIdx.x * 54 + 27 + t], nq, acc);
+        float acc = lin ? 0.f : b1[threadIdx.x];
+        if (!lin)
+            for (int t = 0; t < 27; ++t) acc = fmaf(W1q[threadIdx.x * 54 + 27 + t], nq, acc);
         beff[threadIdx.x] = acc;
     }
     __syncthreads();
@@ -149,7 +157,7 @@ net_in_fwd(const TU *__restrict__ u, int m, int sx, int sy, int sz, const float 
     }
     __align__(16) bf16 o[16];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(gelu_f(acc[c]));
+    for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(lin ? acc[c] : gelu_f(acc[c]));
     uint4 *ap = reinterpret_cast<uint4 *>(a1 + 16 * p);
     ap[0] = reinterpret_cast<const uint4 *>(o)[0];
     ap[1] = reinterpret_cast<const uint4 *>(o)[1];
@@ -159,11 +167,12 @@ net_in_fwd(const TU *__restrict__ u, int m, int sx, int sy, int sz, const float 
 
 // MODE 0 (forward):  out = bf16(gelu(acc + bias)), zout = acc + bias (if non-null)
 // MODE 1 (dgrad):    out = bf16(acc * gelu'(zaux))
+// (linear mode: no bias, identity activation, so out = bf16(acc) in both)
 // acc[p][n] = sum_tap sum_k in[p + tap][k] * Bt[tap][n][k]
 template <int MODE>
 __global__ void __launch_bounds__(256)
 net_mid(const bf16 *__restrict__ in, int m, const bf16 *__restrict__ Bt, const float *__restrict__ bias,
-        const float *__restrict__ zaux, float *__restrict__ zout, bf16 *__restrict__ out)
+        const float *__restrict__ zaux, float *__restrict__ zout, bf16 *__restrict__ out, int lin)
 {
     extern __shared__ uint4 sm_mid[];
     uint4 *act = sm_mid;               // 2000 chunks: [1000 points][2]
@@ -214,7 +223,10 @@ net_mid(const bf16 *__restrict__ in, int m, const bf16 *__restrict__ Bt, const f
             for (int nt = 0; nt < 2; ++nt) {
                 const int co = nt * 8 + 2 * tq;
                 float v0 = acc[mt][nt][2 * hh], v1 = acc[mt][nt][2 * hh + 1];
-                if (MODE == 0) {
+                if (lin) {
+                    if (MODE == 0 && zout)
+                        *reinterpret_cast<float2 *>(zout + 16 * p + co) = make_float2(v0, v1);
+                } else if (MODE == 0) {
                     v0 += bias[co];
                     v1 += bias[co + 1];
                     if (zout) *reinterpret_cast<float2 *>(zout + 16 * p + co) = make_float2(v0, v1);
@@ -322,7 +334,7 @@ __global__ void __launch_bounds__(512)
 net_out_fwd(const bf16 *__restrict__ a3, int m, const float *__restrict__ W4q, const float *__restrict__ b4,
             const TU *__restrict__ u, int sx, int sy, int sz, TG *__restrict__ g_out,
             const float *__restrict__ tgt, float grad_scale, bf16 *__restrict__ dz4,
-            double *__restrict__ loss_partials)
+            double *__restrict__ loss_partials, int lin)
 {
     extern __shared__ uint4 sm_out[];
     uint4 *act = sm_out;                                    // 2000 chunks
@@ -335,7 +347,7 @@ net_out_fwd(const bf16 *__restrict__ a3, int m, const float *__restrict__ W4q, c
     for (int i = threadIdx.x; i < 432; i += blockDim.x) w[i] = W4q[i];
     __syncthreads();
     const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;
-    float acc = b4[0];
+    float acc = lin ? 0.f : b4[0];
     for (int t = 0; t < 27; ++t) {
         const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
         const int q = ((lz + 1 + dz) * 10 + (ly + 1 + dy)) * 10 + lx + 1 + dx;
@@ -370,7 +382,7 @@ net_out_fwd(const bf16 *__restrict__ a3, int m, const float *__restrict__ W4q, c
 // dz3[p][ci] = bf16( (sum_tap dz4[p - tap] W4[ci][tap]) * gelu'(z3[p][ci]) )
 __global__ void __launch_bounds__(512)
 net_out_dgrad(const bf16 *__restrict__ dz4, int m, const float *__restrict__ W4q,
-              const float *__restrict__ z3, bf16 *__restrict__ dz3)
+              const float *__restrict__ z3, bf16 *__restrict__ dz3, int lin)
 {
     __shared__ float ds[1000];
     __shared__ float w[432];
@@ -399,11 +411,11 @@ net_out_dgrad(const bf16 *__restrict__ dz4, int m, const float *__restrict__ W4q
     __align__(16) bf16 o[16];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        const float4 zz = zp[c];
-        o[4 * c + 0] = __float2bfloat16_rn(acc[4 * c + 0] * gelu_grad_f(zz.x));
-        o[4 * c + 1] = __float2bfloat16_rn(acc[4 * c + 1] * gelu_grad_f(zz.y));
-        o[4 * c + 2] = __float2bfloat16_rn(acc[4 * c + 2] * gelu_grad_f(zz.z));
-        o[4 * c + 3] = __float2bfloat16_rn(acc[4 * c + 3] * gelu_grad_f(zz.w));
+        const float4 zz = lin ? make_float4(0.f, 0.f, 0.f, 0.f) : zp[c];
+        o[4 * c + 0] = __float2bfloat16_rn(lin ? acc[4 * c + 0] : acc[4 * c + 0] * gelu_grad_f(zz.x));
+        o[4 * c + 1] = __float2bfloat16_rn(lin ? acc[4 * c + 1] : acc[4 * c + 1] * gelu_grad_f(zz.y));
+        o[4 * c + 2] = __float2bfloat16_rn(lin ? acc[4 * c + 2] : acc[4 * c + 2] * gelu_grad_f(zz.z));
+        o[4 * c + 3] = __float2bfloat16_rn(lin ? acc[4 * c + 3] : acc[4 * c + 3] * gelu_grad_f(zz.w));
     }
     uint4 *op = reinterpret_cast<uint4 *>(dz3 + 16 * p);
     op[0] = reinterpret_cast<const uint4 *>(o)[0];
@@ -452,11 +464,12 @@ net_out_wgrad(const bf16 *__restrict__ a3, const bf16 *__restrict__ dz4, int m, 
 
 // dW1[co][0][tap] = sum_p x0[p + tap] dz1[p][co]   (x0 = bf16(S(u)))
 // dW1[co][1][tap] = sum_samples bf16(nu_hat_s) sum_p dz1[p][co],  db1[co] = sum_p dz1[p][co]
+// (linear mode: dW1[co][1][tap] = sum_samples bf16(nu_hat_s) sum_p x0[p + tap] dz1[p][co])
 // partial layout: [16][2][27] then [16] (NET_IN_PARTIAL = 880 floats).
 template <typename TU>
 __global__ void __launch_bounds__(448)
 net_in_wgrad(const TU *__restrict__ u, int m, int sx, int sy, int sz, const float *__restrict__ nu_hat,
-             const bf16 *__restrict__ dz1, int tiles_total, float *__restrict__ partials)
+             const bf16 *__restrict__ dz1, int tiles_total, float *__restrict__ partials, int lin)
 {
     __shared__ float xs[1000];
     __shared__ float ds[512 * 17];    // [point][16] padded to 17
@@ -484,10 +497,13 @@ net_in_wgrad(const TU *__restrict__ u, int m, int sx, int sy, int sz, const floa
         __syncthreads();
         if (threadIdx.x < 432) {
             const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+            float part = 0.f;
             for (int q = 0; q < 512; ++q) {
                 const int lx = q & 7, ly = (q >> 3) & 7, lz = q >> 6;
-                acc = fmaf(xs[((lz + 1 + dz) * 10 + (ly + 1 + dy)) * 10 + lx + 1 + dx], ds[q * 17 + co], acc);
+                part = fmaf(xs[((lz + 1 + dz) * 10 + (ly + 1 + dy)) * 10 + lx + 1 + dx], ds[q * 17 + co], part);
             }
+            acc += part;
+            if (lin) accnu = fmaf(bf16r(nu_hat[s]), part, accnu);
         } else if (threadIdx.x < 448) {
             const int c = threadIdx.x - 432;
             float sum = 0.f;
@@ -499,9 +515,11 @@ net_in_wgrad(const TU *__restrict__ u, int m, int sx, int sy, int sz, const floa
     float *out = partials + (long long)blockIdx.x * NET_IN_PARTIAL;
     if (threadIdx.x < 432) {
         out[co * 54 + t] = acc;
+        if (lin) out[co * 54 + 27 + t] = accnu;
     } else if (threadIdx.x < 448) {
         const int c = threadIdx.x - 432;
-        for (int k = 0; k < 27; ++k) out[c * 54 + 27 + k] = accnu;
+        if (!lin)
+            for (int k = 0; k < 27; ++k) out[c * 54 + 27 + k] = accnu;
         out[864 + c] = accb;
     }
 }
@@ -569,15 +587,19 @@ static unsigned tiles_of(int m) { return (unsigned)((m / 8) * (m / 8) * (m / 8))
 
 template <typename TU>
 cudaError_t launch_net_in_fwd(const TU *u, int m, const int s[3], const float *nu_hat, int batch,
-                              const float *W1q, const float *b1, float *z1, bf16 *a1, cudaStream_t st)
+                              const float *W1q, const float *b1, float *z1, bf16 *a1, cudaStream_t st,
+                              int lin)
 {
-    net_in_fwd<TU><<<dim3(tiles_of(m), batch), 512, 0, st>>>(u, m, s[0], s[1], s[2], nu_hat, W1q, b1, z1, a1);
+    net_in_fwd<TU><<<dim3(tiles_of(m), batch), 512, 0, st>>>(u, m, s[0], s[1], s[2], nu_hat, W1q, b1, z1, a1,
+                                                             lin);
     return cudaGetLastError();
 }
 template cudaError_t launch_net_in_fwd<float>(const float *, int, const int *, const float *, int,
-                                              const float *, const float *, float *, bf16 *, cudaStream_t);
+                                              const float *, const float *, float *, bf16 *, cudaStream_t,
+                                              int);
 template cudaError_t launch_net_in_fwd<double>(const double *, int, const int *, const float *, int,
-                                               const float *, const float *, float *, bf16 *, cudaStream_t);
+                                               const float *, const float *, float *, bf16 *, cudaStream_t,
+                                               int);
 
 static constexpr size_t MID_SMEM = (2000 + 864) * 16;
 static constexpr size_t WG_SMEM = (2000 + 1024) * 16;
@@ -599,12 +621,12 @@ cudaError_t configure_net_kernels()
 }
 
 cudaError_t launch_net_mid(int mode, const bf16 *in, int m, int batch, const bf16 *Bt, const float *bias,
-                           const float *zaux, float *zout, bf16 *out, cudaStream_t st)
+                           const float *zaux, float *zout, bf16 *out, cudaStream_t st, int lin)
 {
     if (mode == 0)
-        net_mid<0><<<dim3(tiles_of(m), batch), 256, MID_SMEM, st>>>(in, m, Bt, bias, zaux, zout, out);
+        net_mid<0><<<dim3(tiles_of(m), batch), 256, MID_SMEM, st>>>(in, m, Bt, bias, zaux, zout, out, lin);
     else
-        net_mid<1><<<dim3(tiles_of(m), batch), 256, MID_SMEM, st>>>(in, m, Bt, bias, zaux, zout, out);
+        net_mid<1><<<dim3(tiles_of(m), batch), 256, MID_SMEM, st>>>(in, m, Bt, bias, zaux, zout, out, lin);
     return cudaGetLastError();
 }
 
@@ -624,29 +646,29 @@ cudaError_t launch_net_mid_wgrad(const bf16 *x, const bf16 *dz, int m, int batch
 template <typename TU, typename TG>
 cudaError_t launch_net_out_fwd(const bf16 *a3, int m, int batch, const float *W4q, const float *b4,
                                const TU *u, const int s[3], TG *g_out, const float *tgt, float grad_scale,
-                               bf16 *dz4, double *loss_partials, cudaStream_t st)
+                               bf16 *dz4, double *loss_partials, cudaStream_t st, int lin)
 {
     net_out_fwd<TU, TG><<<dim3(tiles_of(m), batch), 512, OUT_SMEM, st>>>(
-        a3, m, W4q, b4, u, s[0], s[1], s[2], g_out, tgt, grad_scale, dz4, loss_partials);
+        a3, m, W4q, b4, u, s[0], s[1], s[2], g_out, tgt, grad_scale, dz4, loss_partials, lin);
     return cudaGetLastError();
 }
 template cudaError_t launch_net_out_fwd<float, float>(const bf16 *, int, int, const float *, const float *,
                                                       const float *, const int *, float *, const float *,
-                                                      float, bf16 *, double *, cudaStream_t);
+                                                      float, bf16 *, double *, cudaStream_t, int);
 template cudaError_t launch_net_out_fwd<double, double>(const bf16 *, int, int, const float *, const float *,
                                                         const double *, const int *, double *, const float *,
-                                                        float, bf16 *, double *, cudaStream_t);
+                                                        float, bf16 *, double *, cudaStream_t, int);
 template cudaError_t launch_net_out_fwd<float, double>(const bf16 *, int, int, const float *, const float *,
                                                        const float *, const int *, double *, const float *,
-                                                       float, bf16 *, double *, cudaStream_t);
+                                                       float, bf16 *, double *, cudaStream_t, int);
 template cudaError_t launch_net_out_fwd<double, float>(const bf16 *, int, int, const float *, const float *,
                                                        const double *, const int *, float *, const float *,
-                                                       float, bf16 *, double *, cudaStream_t);
+                                                       float, bf16 *, double *, cudaStream_t, int);
 
 cudaError_t launch_net_out_dgrad(const bf16 *dz4, int m, int batch, const float *W4q, const float *z3,
-                                 bf16 *dz3, cudaStream_t st)
+                                 bf16 *dz3, cudaStream_t st, int lin)
 {
-    net_out_dgrad<<<dim3(tiles_of(m), batch), 512, 0, st>>>(dz4, m, W4q, z3, dz3);
+    net_out_dgrad<<<dim3(tiles_of(m), batch), 512, 0, st>>>(dz4, m, W4q, z3, dz3, lin);
     return cudaGetLastError();
 }
 
@@ -659,16 +681,16 @@ cudaError_t launch_net_out_wgrad(const bf16 *a3, const bf16 *dz4, int m, int bat
 
 template <typename TU>
 cudaError_t launch_net_in_wgrad(const TU *u, int m, int batch, const int s[3], const float *nu_hat,
-                                const bf16 *dz1, float *partials, int nblocks, cudaStream_t st)
+                                const bf16 *dz1, float *partials, int nblocks, cudaStream_t st, int lin)
 {
     net_in_wgrad<TU><<<nblocks, 448, 0, st>>>(u, m, s[0], s[1], s[2], nu_hat, dz1,
-                                              (int)tiles_of(m) * batch, partials);
+                                              (int)tiles_of(m) * batch, partials, lin);
     return cudaGetLastError();
 }
 template cudaError_t launch_net_in_wgrad<float>(const float *, int, int, const int *, const float *,
-                                                const bf16 *, float *, int, cudaStream_t);
+                                                const bf16 *, float *, int, cudaStream_t, int);
 template cudaError_t launch_net_in_wgrad<double>(const double *, int, int, const int *, const float *,
-                                                 const bf16 *, float *, int, cudaStream_t);
+                                                 const bf16 *, float *, int, cudaStream_t, int);
 
 cudaError_t launch_reduce_cols(const float *partials, int nb, int stride, int L, float *out, cudaStream_t st)
 {

@@ -6,6 +6,8 @@
 
 namespace pr {
 
+// Linear mode (lin != 0, see net.cu): identity activations, no biases, input
+// channel 2 = nu_hat * S(u).
 // FP32 master parameters, in this order (tap = (dz+1)*9 + (dy+1)*3 + (dx+1)):
 //   W1[16][2][27] b1[16] W2[16][16][27] b2[16] W3[16][16][27] b3[16] W4[1][16][27] b4[1]
 constexpr int NET_W1 = 0, NET_B1 = 864, NET_W2 = 880, NET_B2 = 7792, NET_W3 = 7808,
@@ -18,10 +20,10 @@ cudaError_t configure_net_kernels();
 template <typename TU>
 cudaError_t launch_net_in_fwd(const TU *u, int m, const int s[3], const float *nu_hat, int batch,
                               const float *W1q, const float *b1, float *z1, __nv_bfloat16 *a1,
-                              cudaStream_t st);
+                              cudaStream_t st, int lin = 0);
 cudaError_t launch_net_mid(int mode, const __nv_bfloat16 *in, int m, int batch,
                            const __nv_bfloat16 *Bt, const float *bias, const float *zaux, float *zout,
-                           __nv_bfloat16 *out, cudaStream_t st);
+                           __nv_bfloat16 *out, cudaStream_t st, int lin = 0);
 int net_partial_blocks(int m, int batch);
 cudaError_t launch_net_mid_wgrad(const __nv_bfloat16 *x, const __nv_bfloat16 *dz, int m, int batch,
                                  float *partials, int nblocks, cudaStream_t st);
@@ -29,15 +31,15 @@ template <typename TU, typename TG>
 cudaError_t launch_net_out_fwd(const __nv_bfloat16 *a3, int m, int batch, const float *W4q,
                                const float *b4, const TU *u, const int s[3], TG *g_out,
                                const float *tgt, float grad_scale, __nv_bfloat16 *dz4,
-                               double *loss_partials, cudaStream_t st);
+                               double *loss_partials, cudaStream_t st, int lin = 0);
 cudaError_t launch_net_out_dgrad(const __nv_bfloat16 *dz4, int m, int batch, const float *W4q,
-                                 const float *z3, __nv_bfloat16 *dz3, cudaStream_t st);
+                                 const float *z3, __nv_bfloat16 *dz3, cudaStream_t st, int lin = 0);
 cudaError_t launch_net_out_wgrad(const __nv_bfloat16 *a3, const __nv_bfloat16 *dz4, int m, int batch,
                                  float *partials, int nblocks, cudaStream_t st);
 template <typename TU>
 cudaError_t launch_net_in_wgrad(const TU *u, int m, int batch, const int s[3], const float *nu_hat,
                                 const __nv_bfloat16 *dz1, float *partials, int nblocks,
-                                cudaStream_t st);
+                                cudaStream_t st, int lin = 0);
 cudaError_t launch_reduce_cols(const float *partials, int nb, int stride, int L, float *out,
                                cudaStream_t st);
 cudaError_t launch_reduce_mid(const float *partials, int nb, float *W, float *b, cudaStream_t st);

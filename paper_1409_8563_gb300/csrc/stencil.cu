@@ -249,7 +249,7 @@ __device__ __forceinline__ void fused_step(FusedIter<T> &I, FusedRegs<T> &R, con
         const T(&u4)[V] = R.U[PH % 4];
         const T(&y4c)[V] = R.Y4[(PH + 2) % 3];
         stage_delta<T>(d, Sc + 2 * PL, Ec + 4 * EL, EL, L, y4c, R.Y4[(PH + 1) % 3], y4n, w4);
-        if (I.owner && it >= 8) {
+        if (it >= 8) {
             const T(&y2c)[V] = R.Y2[(PH + 1) % 4];
             const T(&y3c)[V] = R.Y3[(PH + 1) % 3];
             T o[V];
@@ -258,7 +258,7 @@ __device__ __forceinline__ void fused_step(FusedIter<T> &I, FusedRegs<T> &R, con
                 const T s = fma((T)2, y3c[i] - u4[i], (y2c[i] - u4[i]) + (y4c[i] - u4[i]));
                 o[i] = fma(c3, s, fma(c6, d[i], u4[i]));
             }
-            stv<T>(I.dst + I.ooff, o);
+            if (I.owner) stv<T>(I.dst + I.ooff, o);
         }
     }
     I.ooff += I.plane;
@@ -363,10 +363,14 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
     auto active = [&](int s) {
         return ry >= s && ry < RY - s && (qx + 1) * V > s && qx * V < RX - s;
     };
-    I.act1 = active(1);
-    I.act2 = active(2);
-    I.act3 = active(3);
-    I.act4 = active(4);
+    // warp-uniform stage flags: a warp takes a stage when any of its lanes
+    // needs it (the other lanes' results there are never read), so the
+    // stage branches never diverge
+    const unsigned lanes = __activemask();
+    I.act1 = __any_sync(lanes, active(1));
+    I.act2 = __any_sync(lanes, active(2));
+    I.act3 = __any_sync(lanes, active(3));
+    I.act4 = __any_sync(lanes, active(4));
     I.owner = ry >= 4 && ry < 4 + TY && qx * V >= 4 && qx * V < 4 + TX;
 
     // prologue: planes of iterations 0 .. D-1 into ring slots 0 .. D-1

@@ -286,3 +286,125 @@ def test_stencil_skip_training_improves_the_early_iterates():
     assert np.all(np.isfinite(d_learned)) and np.max(d_learned) < 1.0
     ctx.close()
     st.close()
+
+
+# ------------------------------------------------- linear learned propagator
+
+@pytest.mark.parametrize("skip", [native.SKIP_SHIFT, native.SKIP_STENCIL])
+def test_linear_forward_matches_oracle(skip):
+    base, _ = configs.small(n=16, n_slices=4, dtype=native.F32, r=2, nf=8, nc=4)
+    base.coarse_kind = native.COARSE_LEARNED
+    base.learned_skip = skip
+    base.learned_act = native.ACT_LINEAR
+    if skip == native.SKIP_SHIFT:
+        base.coarse_factor = 1
+    ctx = native.Parareal(base)
+    params = net.init_params(seed=8, scale=0.15)
+    for W, b in params:
+        b += 0.25                      # ignored in linear mode
+    w = to_master(params)
+    ctx.set_coarse_model(w)
+    params = from_master(w)
+    u = inputs.spectral_ic(16, seed=12, kmax=4)
+    src = torch.from_numpy(u).cuda().contiguous()
+    dst = torch.empty_like(src)
+    s = 3
+    ctx.propagate(1, src, dst, s, 1)
+    got = dst.cpu().numpy()
+    if skip == native.SKIP_STENCIL:
+        sk, shift = oracle_G_stencil(base)(u, s), (0, 0, 0)
+    else:
+        sk, shift = u, shift_of(base)
+    ref, _ = net.forward(sk, nu_hat(base, s), params, shift, bf16_emul=True, linear=True)
+    base_out = core.shift(sk, shift)
+    assert np.max(np.abs(ref - base_out)) > 1e-2
+    err = rel_l2(got - base_out, ref - base_out)
+    assert err < NET_TOL, err
+    # linear: G(2u) = 2 G(u) up to the bf16 rounding of the network input
+    ctx.propagate(1, 2 * src, dst, s, 1)
+    assert rel_l2(dst.cpu().numpy() - 2 * base_out, 2 * (got - base_out)) < NET_TOL
+    ctx.close()
+
+
+def test_linear_gradients_match_oracle():
+    cfg = learned_cfg()
+    cfg.learned_act = native.ACT_LINEAR
+    ctx = native.Parareal(cfg)
+    params = net.init_params(seed=9, scale=0.15)
+    w = to_master(params)
+    ctx.set_coarse_model(w)
+    params = from_master(w)
+    us = [inputs.spectral_ic(16, seed=40 + i, kmax=4) for i in range(2)]
+    tg = [core.shift(x, shift_of(cfg)) * 0.9 + 0.05 * inputs.spectral_ic(16, seed=50 + i, kmax=6)
+          for i, x in enumerate(us)]
+    us32 = [x.astype(np.float32) for x in us]
+    tg32 = [x.astype(np.float32) for x in tg]
+    slices = [0, 2]
+    U = torch.from_numpy(np.stack(us32)).cuda()
+    Tg = torch.from_numpy(np.stack(tg32)).cuda()
+    g = torch.empty(native.MODEL_PARAMS, dtype=torch.float32, device="cuda")
+    loss = ctx.coarse_model_grad(U, Tg, slices, g)
+    ref_loss, ref_g = net.loss_and_grads([x.astype(np.float64) for x in us32],
+                                         [nu_hat(cfg, s) for s in slices],
+                                         [x.astype(np.float64) for x in tg32], params,
+                                         shift_of(cfg), bf16_emul=True, linear=True)
+    assert abs(loss - ref_loss) <= 1e-3 * ref_loss, (loss, ref_loss)
+    got = from_master(g.cpu().numpy())
+    for li in range(4):
+        e = rel_l2(got[li][0], ref_g[li][0])
+        assert e < 2 * NET_TOL, (li, e)
+        assert not np.any(got[li][1])          # no biases in linear mode
+    ctx.close()
+
+
+def test_difference_form_needs_a_linear_propagator():
+    cfg = learned_cfg()
+    cfg.correction_form = native.CORRECTION_DIFFERENCE
+    with pytest.raises(native.PararealError):
+        native.Parareal(cfg)
+    cfg.learned_act = native.ACT_LINEAR
+    native.Parareal(cfg).close()
+
+
+def _linear_pair_cfg(kind, form):
+    n, N = 32, 8
+    m = max(6, math.ceil(math.log2(12.0 * 0.015 * n * n / 1.5)))
+    dt = 2.0 ** -m
+    return native.Config.make(n, N, 1.0, dt, 1.0 / N / 4, 2, fine_dtype=native.F32,
+                              coarse_kind=kind, learned_skip=native.SKIP_STENCIL,
+                              learned_act=native.ACT_LINEAR, correction_form=form,
+                              nu0=0.01, nu_amp=0.5, nu_omega=2 * math.pi)
+
+
+def test_linear_learned_propagator_beats_the_stencil_propagator():
+    """The linear learned G (stencil skip, nu as a factor) trained on F - Gs,
+    with the correction applied to U^{k+1}[n] - U^k[n]: a smaller defect than
+    the stencil G at every iteration before k = N.  (With the standard form
+    the bf16 rounding of the network input puts a floor under the defect.)"""
+    N = 8
+    ctx = native.Parareal(_linear_pair_cfg(native.COARSE_LEARNED, native.CORRECTION_DIFFERENCE))
+    n = 32
+    ics = np.stack([inputs.spectral_ic(n, seed=100 + i, kmax=n // 2 - 1)
+                    + 0.2 * inputs.random_field(n, seed=200 + i) for i in range(16)]).astype(np.float32)
+    pu = torch.empty((16 * N, n, n, n), dtype=torch.float32, device="cuda")
+    pf = torch.empty_like(pu)
+    sl = ctx.make_pairs(torch.from_numpy(ics).cuda(), pu, pf)
+    ctx.set_coarse_model(inputs.initial_weights(seed=0))
+    hist = ctx.train_coarse(pu, pf, sl, epochs=40, batch=8, lr=2e-3, seed=1)
+    assert hist[-1] < 0.2 * hist[0], hist
+    u0 = torch.from_numpy(inputs.spectral_ic(n, seed=7, kmax=6)).cuda()
+
+    def defects(c):
+        c.set_problem(u0)
+        c.serial_fine(None, as_reference=True)
+        k, h = c.iterate(N, 0.0, native.STOP_NONE)
+        return h[:, 2]
+
+    d_lin = defects(ctx)
+    st = native.Parareal(_linear_pair_cfg(native.COARSE_STENCIL, native.CORRECTION_STANDARD))
+    d_st = defects(st)
+    assert d_lin[-1] == 0.0 and d_st[-1] == 0.0
+    for k in range(N - 1):
+        assert d_lin[k] < d_st[k], (k, d_lin, d_st)
+    ctx.close()
+    st.close()

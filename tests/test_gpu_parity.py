@@ -242,3 +242,28 @@ def test_single_slice_parareal_is_exact_after_one_iteration():
     kd, h = ctx.iterate(5, 0.0, native.STOP_NONE)
     assert kd == 1 and h[0, 2] == 0.0
     ctx.close()
+
+
+@pytest.mark.parametrize("dtype,r", [(F64, 1), (F64, 2), (F32, 2), (F32, 4)])
+def test_difference_form_matches_oracle(monkeypatch, dtype, r):
+    """F(U^k[n]) + G(U^{k+1}[n] - U^k[n]) on the GPU against Eq. (parareal) as
+    printed in the oracle (equal for the linear stencil G), and exact at k = N."""
+    tile_env(monkeypatch)
+    cfg, u0 = configs.small(n=32, n_slices=4, dtype=dtype, r=r, nf=8, nc=2)
+    cfg.correction_form = native.CORRECTION_DIFFERENCE
+    K = 2
+    ctx = native.Parareal(cfg)
+    ctx.set_problem(dev(u0, F64))
+    ctx.iterate(K, 0.0, native.STOP_NONE)
+    got = read_all(ctx, cfg)
+    hist = opr.parareal(oracle_F(cfg), oracle_G(cfg), u0, cfg.n_slices, K)
+    for s in range(1, cfg.n_slices + 1):
+        e = rel_l2(got[s], hist[K][s])
+        assert e < TOL[dtype], (s, e)
+    ctx.set_problem(dev(u0, F64))
+    ctx.iterate(cfg.n_slices, 0.0, native.STOP_NONE)
+    last = read_all(ctx, cfg)[cfg.n_slices]
+    ref = torch.empty((cfg.n,) * 3, dtype=torch.float64, device="cuda")
+    ctx.serial_fine(ref, as_reference=False)
+    assert np.array_equal(last, host(ref))
+    ctx.close()

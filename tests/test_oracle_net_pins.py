@@ -65,3 +65,37 @@ def test_first_adam_step_moves_by_lr_times_sign():
     net.adam_step(params, grads, m, v, 1, lr=0.01, eps=0.0)
     assert np.allclose(params[0][0], [[0.49, -0.99]], atol=1e-15, rtol=0)
     assert np.allclose(params[0][1], [-0.01], atol=1e-15, rtol=0)
+
+
+@pytest.mark.parametrize("layer,idx", [(0, (3, 1, 0, 2, 1)), (0, (9, 0, 1, 1, 2)),
+                                       (1, (5, 7, 2, 2, 0)), (3, (0, 4, 0, 1, 2))])
+def test_linear_mode_gradient_matches_central_differences(layer, idx):
+    """Linear mode: backprop through identity activations and the nu-weighted
+    second channel (index (co, 1, ...) of layer 0) against central differences;
+    the unused biases get zero gradient."""
+    u, tgt = small_problem()
+    params = net.init_params(seed=2, scale=0.2)
+    _, grads = net.loss_and_grads([u], [0.8], [tgt], params, (1, 0, 2), linear=True)
+    eps = 1e-5
+    vals = []
+    for sgn in (+1, -1):
+        p = [[W.copy(), b.copy()] for W, b in params]
+        p[layer][0][idx] += sgn * eps
+        vals.append(net.loss_and_grads([u], [0.8], [tgt], p, (1, 0, 2), linear=True)[0])
+    fd = (vals[0] - vals[1]) / (2 * eps)
+    assert abs(fd - grads[layer][0][idx]) < 1e-7 * max(1.0, abs(fd)), (fd, grads[layer][0][idx])
+    assert not np.any(grads[layer][1])
+
+
+def test_linear_mode_is_linear_in_u_with_a_nu_dependent_kernel():
+    """G(a u + b v) = a G(u) + b G(v) and G(0) = 0, even with nonzero biases;
+    the map changes with nu_hat (nu enters as a factor, not as an offset)."""
+    u, _ = small_problem(seed=4)
+    v, _ = small_problem(seed=7)
+    params = net.init_params(seed=5, scale=0.2)
+    for W, b in params:
+        b += 0.3
+    G = lambda x, nu=0.9: net.forward(x, nu, params, (1, 0, 2), linear=True)[0]
+    assert np.allclose(G(2.0 * u - 0.5 * v), 2.0 * G(u) - 0.5 * G(v), atol=1e-12, rtol=0)
+    assert not np.any(G(np.zeros_like(u)))
+    assert np.max(np.abs(G(u, 0.9) - G(u, 1.3))) > 1e-3

@@ -335,3 +335,22 @@ def test_input_generators_are_seeded_and_normalised():
     ns, nus = inputs.batch_instances(seed=0)
     assert len(ns) == 64 and set(ns) <= {32, 48, 64, 96, 128}
     assert all(0.002 <= v <= 0.02 for v in nus)
+
+
+def test_difference_form_equals_standard_form_for_a_linear_coarse_propagator():
+    """With a linear G, F(U^k[n]) + G(U^{k+1}[n] - U^k[n]) is Eq. (parareal)
+    rearranged: both forms agree to rounding at every iteration, and both are
+    exact at k = N."""
+    n, N = 8, 4
+    P = core.Problem(n, a=(1.0, -0.5, 0.25), nu0=0.01, nu_amp=0.5, nu_omega=2 * np.pi)
+    F = opr.rk4_propagator(P, 1 / 256, 8)
+    G = opr.coarsened_rk4_propagator(P, 2, 1 / 64, 2)
+    u0 = inputs.spectral_ic(n, seed=2, kmax=3)
+    hs = opr.parareal(F, G, u0, N, N)
+    hd = opr.parareal(F, G, u0, N, N, form="difference")
+    scale = np.max(np.abs(u0))
+    for k in range(N + 1):
+        for s in range(N + 1):
+            assert np.max(np.abs(hs[k][s] - hd[k][s])) < 1e-13 * scale, (k, s)
+    fine = opr.serial_fine(F, u0, N)
+    assert np.max(np.abs(hd[N][N] - fine[N])) < 1e-13 * scale
