@@ -154,6 +154,37 @@ __device__ __forceinline__ void stage_delta(T (&d)[VecT<T>::V], const T *__restr
     }
 }
 
+// y[i] = base[i] + (w . stencil)[i]: the weighted 7-point sum of stage_delta
+// accumulated onto base in one FMA chain (the stage's RK4 factor is folded
+// into w).
+template <typename T>
+__device__ __forceinline__ void stage_axpy(T (&y)[VecT<T>::V], const T *__restrict__ Sp,
+                                           const T *__restrict__ E, int EL, const FusedLane &L,
+                                           const T (&c)[VecT<T>::V], const T (&zm)[VecT<T>::V],
+                                           const T (&zp)[VecT<T>::V], const T (&w)[7],
+                                           const T (&base)[VecT<T>::V])
+{
+    constexpr int V = VecT<T>::V;
+    T ym[V], yp[V];
+    ldv<T>(Sp + L.ym, ym);
+    ldv<T>(Sp + L.yp, yp);
+    const T left = E[EL + L.el];
+    const T right = E[L.er];
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        const T l = (i == 0) ? left : c[i - 1];
+        const T r = (i == V - 1) ? right : c[i + 1];
+        T acc = fma(w[0], c[i], base[i]);
+        acc = fma(w[1], l, acc);
+        acc = fma(w[2], r, acc);
+        acc = fma(w[3], ym[i], acc);
+        acc = fma(w[4], yp[i], acc);
+        acc = fma(w[5], zm[i], acc);
+        acc = fma(w[6], zp[i], acc);
+        y[i] = acc;
+    }
+}
+
 // Elementwise helpers over a thread's vector: z = fma(a, x, y), z = x + y.
 template <typename T>
 __device__ __forceinline__ void vfma(T (&z)[VecT<T>::V], T a, const T (&x)[VecT<T>::V],
@@ -205,7 +236,7 @@ __device__ __forceinline__ void fused_step(FusedIter<T> &I, FusedRegs<T> &R, con
 {
     using S = FusedShape<T, TX, TY>;
     constexpr int V = S::V, PL = S::PL, EL = S::EL, D = S::D, RING = S::RING;
-    constexpr T c6 = (T)(1.0 / 6.0), c3 = (T)(1.0 / 3.0), hf = (T)0.5;
+    constexpr T c3 = (T)(1.0 / 3.0);
     if (it >= I.n_it) return;
     // request the u plane of iteration it + D
     if (it + D < I.n_it)
@@ -227,39 +258,38 @@ __device__ __forceinline__ void fused_step(FusedIter<T> &I, FusedRegs<T> &R, con
     T *Sn = I.planes + ((PH + 1) & 1) * 3 * PL;
     T *En = I.eplanes + ((PH + 1) & 1) * 6 * EL;
 
-    T d[V];
+    // w1, w2 carry the factor 1/2 of y2 = u + d1/2 and y3 = u + d2/2, w4 the
+    // factor 1/6 of d4 in the result, so each stage is one FMA chain
     T y2n[V] = {}, y3n[V] = {}, y4n[V] = {};
     // stage 1 at the plane of iteration it-1
-    if (I.act1) {
-        stage_delta<T>(d, Su, Eu, EL, L, R.U[(PH + 3) % 4], R.U[(PH + 2) % 4], un, w1);
-        vfma<T>(y2n, hf, d, R.U[(PH + 3) % 4]);
-    }
+    if (I.act1)
+        stage_axpy<T>(y2n, Su, Eu, EL, L, R.U[(PH + 3) % 4], R.U[(PH + 2) % 4], un, w1,
+                      R.U[(PH + 3) % 4]);
     // stage 2 at the plane of iteration it-2
-    if (I.act2) {
-        stage_delta<T>(d, Sc, Ec, EL, L, R.Y2[(PH + 3) % 4], R.Y2[(PH + 2) % 4], y2n, w2);
-        vfma<T>(y3n, hf, d, R.U[(PH + 2) % 4]);
-    }
-    // stage 3 at the plane of iteration it-3
+    if (I.act2)
+        stage_axpy<T>(y3n, Sc, Ec, EL, L, R.Y2[(PH + 3) % 4], R.Y2[(PH + 2) % 4], y2n, w2,
+                      R.U[(PH + 2) % 4]);
+    // stage 3 at the plane of iteration it-3: y4 = u + d3 = u + 2 (d3 / 2)
     if (I.act3) {
-        stage_delta<T>(d, Sc + PL, Ec + 2 * EL, EL, L, R.Y3[(PH + 2) % 3], R.Y3[(PH + 1) % 3], y3n, w2);
-        vadd<T>(y4n, R.U[(PH + 1) % 4], d);
+        T h[V];
+        stage_delta<T>(h, Sc + PL, Ec + 2 * EL, EL, L, R.Y3[(PH + 2) % 3], R.Y3[(PH + 1) % 3], y3n, w2);
+        vfma<T>(y4n, (T)2, h, R.U[(PH + 1) % 4]);
     }
     // stage 4 at the plane of iteration it-4: the finished step
-    if (I.act4) {
+    //   u' = u + ((y2 - u) + 2 (y3 - u) + (y4 - u)) / 3 + d4 / 6
+    if (I.act4 && it >= 8) {
         const T(&u4)[V] = R.U[PH % 4];
+        const T(&y2c)[V] = R.Y2[(PH + 1) % 4];
+        const T(&y3c)[V] = R.Y3[(PH + 1) % 3];
         const T(&y4c)[V] = R.Y4[(PH + 2) % 3];
-        stage_delta<T>(d, Sc + 2 * PL, Ec + 4 * EL, EL, L, y4c, R.Y4[(PH + 1) % 3], y4n, w4);
-        if (it >= 8) {
-            const T(&y2c)[V] = R.Y2[(PH + 1) % 4];
-            const T(&y3c)[V] = R.Y3[(PH + 1) % 3];
-            T o[V];
+        T b[V], o[V];
 #pragma unroll
-            for (int i = 0; i < V; ++i) {
-                const T s = fma((T)2, y3c[i] - u4[i], (y2c[i] - u4[i]) + (y4c[i] - u4[i]));
-                o[i] = fma(c3, s, fma(c6, d[i], u4[i]));
-            }
-            if (I.owner) stv<T>(I.dst + I.ooff, o);
+        for (int i = 0; i < V; ++i) {
+            const T s = fma((T)2, y3c[i] - u4[i], (y2c[i] - u4[i]) + (y4c[i] - u4[i]));
+            b[i] = fma(c3, s, u4[i]);
         }
+        stage_axpy<T>(o, Sc + 2 * PL, Ec + 4 * EL, EL, L, y4c, R.Y4[(PH + 1) % 3], y4n, w4, b);
+        if (I.owner) stv<T>(I.dst + I.ooff, o);
     }
     I.ooff += I.plane;
     stv<T>(Sn + L.own, y2n);
@@ -324,8 +354,11 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
         const double ts = a.frozen ? t : (tid == 0 ? t : (tid == 1 ? t + 0.5 * a.dt : t + a.dt));
         double w[7];
         stage_weights(nu_at(a, ts), a.dt, n, a.a, w);
+        // the stage factors of the fused step: 1/2 (stage 1, and stages 2-3,
+        // where stage 3 doubles it back), 1/6 (stage 4)
+        const double f = tid == 2 ? 1.0 / 6.0 : 0.5;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) s_w[tid][k] = (T)w[k];
+        for (int k = 0; k < 7; ++k) s_w[tid][k] = (T)(f * w[k]);
     }
     __syncthreads();
     T w1[7], w2[7], w4[7];
