@@ -810,6 +810,8 @@ extern "C" parareal_status parareal_iterate(parareal_ctx *c, int k_max, double t
         s = iter_enqueue(c);
         if (s != PARAREAL_OK) return s;
         CK(cudaStreamSynchronize(c->st));
+        s = net_check(c);
+        if (s != PARAREAL_OK) return s;
         double dmax, l2max, d;
         s = iter_finish(c, &dmax, &l2max, &d);
         if (s != PARAREAL_OK) return s;
@@ -994,7 +996,8 @@ extern "C" parareal_status parareal_propagate(parareal_ctx *c, int which, const 
     if (!src || !dst || (which != 0 && which != 1)) return fail(c, PARAREAL_E_INVALID, "arguments");
     if (dtype != PARAREAL_F32 && dtype != PARAREAL_F64) return fail(c, PARAREAL_E_INVALID, "dtype");
     if (first < 0 || count < 0 || first + count > c->N) return fail(c, PARAREAL_E_INVALID, "slice range");
-    return DISPATCH(c, propagate_t, which, src, dst, dtype, first, count);
+    parareal_status s = DISPATCH(c, propagate_t, which, src, dst, dtype, first, count);
+    return s != PARAREAL_OK ? s : net_check(c);
 }
 
 // ----------------------------------------------------------------- autotune

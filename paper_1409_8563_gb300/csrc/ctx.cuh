@@ -19,7 +19,7 @@ struct NetState {
     int bmax = 0;              // batch capacity of the training buffers
     float *master = nullptr, *grad = nullptr, *mom1 = nullptr, *mom2 = nullptr;
     float *W1q = nullptr, *W4q = nullptr;
-    __nv_bfloat16 *B2f = nullptr, *B3f = nullptr, *B2b = nullptr, *B3b = nullptr;
+    __nv_bfloat16 *B2f = nullptr, *B3f = nullptr, *B2b = nullptr, *B3b = nullptr, *B4f = nullptr;
     float *nu_slices = nullptr;               // nu(t_n)/nu0 per slice
     __nv_bfloat16 *ia = nullptr, *ib = nullptr;   // inference activations, 1 field each
     // training buffers (bmax fields each)
@@ -33,6 +33,8 @@ struct NetState {
     double *h_loss = nullptr;
     int adam_t = 0;
     int lin = 0;               // linear mode (PARAREAL_ACT_LINEAR)
+    bool tc = false;           // 16 -> 16 layers on tcgen05 (grid edge a multiple of 16)
+    int *tc_err = nullptr;     // device flag: a tensor-core completion wait ran out
     bool has_model = false;
 };
 
@@ -120,6 +122,7 @@ parareal_status iter_finish(parareal_ctx *c, double *dmax, double *l2max, double
 parareal_status stencil_g_fine(parareal_ctx *c, const double *u, int s, double *out);
 
 // learned.cu
+parareal_status net_check(parareal_ctx *c);
 parareal_status net_setup(parareal_ctx *c);
 void net_free(parareal_ctx *c);
 template <typename TU, typename TG>

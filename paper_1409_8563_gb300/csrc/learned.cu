@@ -52,11 +52,14 @@ parareal_status net_setup(parareal_ctx *c)
         S.shift[d] = (int)(((k % S.m) + S.m) % S.m);
     }
     CK(configure_net_kernels());
+    S.tc = net_tc_supported(S.m);
+    if (S.tc) CK(configure_net_tc());
     bool ok = dalloc((void **)&S.master, NET_PARAMS * 4) && dalloc((void **)&S.grad, NET_PARAMS * 4) &&
               dalloc((void **)&S.mom1, NET_PARAMS * 4) && dalloc((void **)&S.mom2, NET_PARAMS * 4) &&
               dalloc((void **)&S.W1q, 864 * 4) && dalloc((void **)&S.W4q, 432 * 4) &&
               dalloc((void **)&S.B2f, 6912 * 2) && dalloc((void **)&S.B3f, 6912 * 2) &&
               dalloc((void **)&S.B2b, 6912 * 2) && dalloc((void **)&S.B3b, 6912 * 2) &&
+              dalloc((void **)&S.B4f, 27 * 8 * 16 * 2) && dalloc((void **)&S.tc_err, sizeof(int)) &&
               dalloc((void **)&S.nu_slices, sizeof(float) * c->N) &&
               dalloc((void **)&S.ia, (size_t)S.Pm * 32) && dalloc((void **)&S.ib, (size_t)S.Pm * 32);
     if (!ok) return fail(c, PARAREAL_E_NOMEM, "learned propagator allocation failed");
@@ -65,9 +68,10 @@ parareal_status net_setup(parareal_ctx *c)
     CK(cudaMemcpy(S.nu_slices, nus.data(), sizeof(float) * c->N, cudaMemcpyHostToDevice));
     // Net = 0 until a model is set: G = S (the shift-only propagator)
     CK(cudaMemsetAsync(S.master, 0, NET_PARAMS * 4, c->st));
+    CK(cudaMemsetAsync(S.tc_err, 0, sizeof(int), c->st));
     CK(cudaMemsetAsync(S.mom1, 0, NET_PARAMS * 4, c->st));
     CK(cudaMemsetAsync(S.mom2, 0, NET_PARAMS * 4, c->st));
-    LK(launch_prepare_operands(S.master, S.W1q, S.B2f, S.B3f, S.B2b, S.B3b, S.W4q, c->st));
+    LK(launch_prepare_operands(S.master, S.W1q, S.B2f, S.B3f, S.B2b, S.B3b, S.W4q, S.B4f, c->st));
     S.has_model = c->cfg.coarse_kind == PARAREAL_COARSE_SHIFT;
     return PARAREAL_OK;
 }
@@ -75,7 +79,7 @@ parareal_status net_setup(parareal_ctx *c)
 void net_free(parareal_ctx *c)
 {
     NetState &S = c->net;
-    void *p[] = {S.master, S.grad, S.mom1, S.mom2, S.W1q, S.W4q, S.B2f, S.B3f, S.B2b, S.B3b,
+    void *p[] = {S.master, S.grad, S.mom1, S.mom2, S.W1q, S.W4q, S.B2f, S.B3f, S.B2b, S.B3b, S.B4f, S.tc_err,
                  S.nu_slices, S.ia, S.ib, S.z1, S.z2, S.z3, S.a1, S.a2, S.a3, S.dzA, S.dzB, S.dz4,
                  S.ub, S.fb, S.nub, S.partials, S.loss_parts, S.loss_sum};
     for (void *q : p)
@@ -83,6 +87,18 @@ void net_free(parareal_ctx *c)
     if (S.h_nub) cudaFreeHost(S.h_nub);
     if (S.h_loss) cudaFreeHost(S.h_loss);
     S = NetState();
+}
+
+// Status of the tensor-core layers since the last check (synchronises the stream).
+parareal_status net_check(parareal_ctx *c)
+{
+    NetState &S = c->net;
+    if (!S.tc || !S.tc_err) return PARAREAL_OK;
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, S.tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (h) return fail(c, PARAREAL_E_TIMEOUT, "tensor-core completion wait ran out in the learned propagator");
+    return PARAREAL_OK;
 }
 
 // G for one field of slice `slice`: u on the net's grid (TU), out on it (TG).
@@ -93,10 +109,14 @@ parareal_status net_apply(parareal_ctx *c, const TU *u, int slice, TG *out)
     const float *b = S.master;
     LK(launch_net_in_fwd<TU>(u, S.m, S.shift, S.nu_slices + slice, 1, S.W1q, b + NET_B1, nullptr, S.ia, c->st,
                              S.lin));
-    LK(launch_net_mid(0, S.ia, S.m, 1, S.B2f, b + NET_B2, nullptr, nullptr, S.ib, c->st, S.lin));
-    LK(launch_net_mid(0, S.ib, S.m, 1, S.B3f, b + NET_B3, nullptr, nullptr, S.ia, c->st, S.lin));
-    LK((launch_net_out_fwd<TU, TG>(S.ia, S.m, 1, S.W4q, b + NET_B4, u, S.shift, out, nullptr, 0.f,
-                                   nullptr, nullptr, c->st, S.lin)));
+    if (S.tc) {
+        LK(launch_net_mid_tc(S.ia, S.m, 1, S.B2f, b + NET_B2, S.ib, S.lin, S.tc_err, c->st));
+        LK(launch_net_mid_tc(S.ib, S.m, 1, S.B3f, b + NET_B3, S.ia, S.lin, S.tc_err, c->st));
+    } else {
+        LK(launch_net_mid(0, S.ia, S.m, 1, S.B2f, b + NET_B2, nullptr, nullptr, S.ib, c->st, S.lin));
+        LK(launch_net_mid(0, S.ib, S.m, 1, S.B3f, b + NET_B3, nullptr, nullptr, S.ia, c->st, S.lin));
+    }
+    LK((launch_net_out_mma<TU, TG>(S.ia, S.m, 1, S.B4f, b + NET_B4, u, S.shift, out, c->st, S.lin)));
     return PARAREAL_OK;
 }
 template parareal_status net_apply<double, double>(parareal_ctx *, const double *, int, double *);
@@ -215,7 +235,7 @@ extern "C" parareal_status parareal_set_coarse_model(parareal_ctx *c, const floa
     CK(cudaMemsetAsync(S.mom1, 0, NET_PARAMS * 4, c->st));
     CK(cudaMemsetAsync(S.mom2, 0, NET_PARAMS * 4, c->st));
     S.adam_t = 0;
-    LK(launch_prepare_operands(S.master, S.W1q, S.B2f, S.B3f, S.B2b, S.B3b, S.W4q, c->st));
+    LK(launch_prepare_operands(S.master, S.W1q, S.B2f, S.B3f, S.B2b, S.B3b, S.W4q, S.B4f, c->st));
     if (mem == PARAREAL_MEM_HOST) CK(cudaStreamSynchronize(c->st));
     S.has_model = true;
     c->started = false;   // G changed: the next iterate restarts from the coarse chain
@@ -308,7 +328,7 @@ extern "C" parareal_status parareal_train_coarse(parareal_ctx *c, const float *p
             const double c2 = 1.0 - std::pow(tc->beta2, S.adam_t);
             LK(launch_adam(S.master, S.grad, S.mom1, S.mom2, NET_PARAMS, (float)tc->lr, (float)tc->beta1,
                            (float)tc->beta2, (float)tc->eps, (float)c1, (float)c2, c->st));
-            LK(launch_prepare_operands(S.master, S.W1q, S.B2f, S.B3f, S.B2b, S.B3b, S.W4q, c->st));
+            LK(launch_prepare_operands(S.master, S.W1q, S.B2f, S.B3f, S.B2b, S.B3b, S.W4q, S.B4f, c->st));
         }
         CK(cudaMemcpyAsync(S.h_loss, S.loss_sum, sizeof(double) * nbat, cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));

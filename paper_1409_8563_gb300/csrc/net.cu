@@ -71,6 +71,12 @@ __device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned (&r)[4])
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                  : "r"(addr));
 }
+__device__ __forceinline__ void ldsm_x2(unsigned addr, unsigned (&r)[2])
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+                 : "=r"(r[0]), "=r"(r[1])
+                 : "r"(addr));
+}
 __device__ __forceinline__ void ldsm_x4_t(unsigned addr, unsigned (&r)[4])
 {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
@@ -105,14 +111,16 @@ __device__ __forceinline__ void load_halo16(uint4 *sm, const bf16 *__restrict__ 
 // z1 = conv(x0, W1) + b1, a1 = bf16(gelu(z1)), x0 = [bf16(S(u)), bf16(nu_hat)].
 // Linear mode: x0 = [bf16(S(u)), bf16(nu_hat) bf16(S(u))], no bias, a1 = bf16(z1);
 // the two channels share their input, so their weights are combined per sample.
+// 128 threads per 8^3 tile, 4 consecutive x points per thread, so each weight
+// read from shared memory feeds four FMAs.
 template <typename TU>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(128)
 net_in_fwd(const TU *__restrict__ u, int m, int sx, int sy, int sz, const float *__restrict__ nu_hat,
            const float *__restrict__ W1q, const float *__restrict__ b1, float *__restrict__ z1,
            bf16 *__restrict__ a1, int lin)
 {
     __shared__ float xs[1000];
-    __shared__ float w[16 * 27];
+    __shared__ __align__(16) float w[27 * 16];     // [tap][channel]
     __shared__ float beff[16];
     const int s = blockIdx.y;
     const long long P = (long long)m * m * m;
@@ -128,7 +136,7 @@ net_in_fwd(const TU *__restrict__ u, int m, int sx, int sy, int sz, const float 
     const float nq = bf16r(nu_hat[s]);
     for (int i = threadIdx.x; i < 16 * 27; i += blockDim.x) {
         const int c = i / 27, t = i % 27;
-        w[i] = lin ? fmaf(nq, W1q[c * 54 + 27 + t], W1q[c * 54 + t]) : W1q[c * 54 + t];
+        w[t * 16 + c] = lin ? fmaf(nq, W1q[c * 54 + 27 + t], W1q[c * 54 + t]) : W1q[c * 54 + t];
     }
     if (threadIdx.x < 16) {
         float acc = lin ? 0.f : b1[threadIdx.x];
@@ -137,30 +145,50 @@ net_in_fwd(const TU *__restrict__ u, int m, int sx, int sy, int sz, const float 
         beff[threadIdx.x] = acc;
     }
     __syncthreads();
-    const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;
-    float acc[16];
+    const int lx0 = (threadIdx.x & 1) * 4, ly = (threadIdx.x >> 1) & 7, lz = threadIdx.x >> 4;
+    float acc[4][16];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = beff[c];
-#pragma unroll 3
-    for (int t = 0; t < 27; ++t) {
-        const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-        const float v = xs[((lz + 1 + dz) * 10 + (ly + 1 + dy)) * 10 + lx + 1 + dx];
+    for (int k = 0; k < 4; ++k)
 #pragma unroll
-        for (int c = 0; c < 16; ++c) acc[c] = fmaf(w[c * 27 + t], v, acc[c]);
+        for (int c = 0; c < 16; ++c) acc[k][c] = beff[c];
+    for (int dz = 0; dz < 3; ++dz)
+        for (int dy = 0; dy < 3; ++dy) {
+            const float *row = xs + ((lz + dz) * 10 + (ly + dy)) * 10 + lx0;
+            float v[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) v[i] = row[i];
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const float4 *wt = reinterpret_cast<const float4 *>(w + ((dz * 3 + dy) * 3 + dx) * 16);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 wq = wt[q];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        acc[k][4 * q + 0] = fmaf(wq.x, v[k + dx], acc[k][4 * q + 0]);
+                        acc[k][4 * q + 1] = fmaf(wq.y, v[k + dx], acc[k][4 * q + 1]);
+                        acc[k][4 * q + 2] = fmaf(wq.z, v[k + dx], acc[k][4 * q + 2]);
+                        acc[k][4 * q + 3] = fmaf(wq.w, v[k + dx], acc[k][4 * q + 3]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const long long p = s * P + ((long long)(T.oz + lz) * m + (T.oy + ly)) * m + T.ox + lx0 + k;
+        if (z1) {
+            float4 *zp = reinterpret_cast<float4 *>(z1 + 16 * p);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                zp[c] = make_float4(acc[k][4 * c], acc[k][4 * c + 1], acc[k][4 * c + 2], acc[k][4 * c + 3]);
+        }
+        __align__(16) bf16 o[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(lin ? acc[k][c] : gelu_f(acc[k][c]));
+        uint4 *ap = reinterpret_cast<uint4 *>(a1 + 16 * p);
+        ap[0] = reinterpret_cast<const uint4 *>(o)[0];
+        ap[1] = reinterpret_cast<const uint4 *>(o)[1];
     }
-    const long long p = s * P + ((long long)(T.oz + lz) * m + (T.oy + ly)) * m + T.ox + lx;
-    if (z1) {
-        float4 *zp = reinterpret_cast<float4 *>(z1 + 16 * p);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            zp[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
-    }
-    __align__(16) bf16 o[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(lin ? acc[c] : gelu_f(acc[c]));
-    uint4 *ap = reinterpret_cast<uint4 *>(a1 + 16 * p);
-    ap[0] = reinterpret_cast<const uint4 *>(o)[0];
-    ap[1] = reinterpret_cast<const uint4 *>(o)[1];
 }
 
 // --------------------------------------------------------- 16 -> 16 layers
@@ -326,6 +354,66 @@ net_mid_wgrad(const bf16 *__restrict__ x, const bf16 *__restrict__ dz, int m, in
 }
 
 // ---------------------------------------------------------------- layer 4
+
+// Inference form of the last layer on the tensor cores: the 16 -> 1
+// convolution as an implicit GEMM with N = 8 (output channel 0; B rows 1-7
+// are zero), the same tiling as net_mid, and the epilogue
+// g = S(u) + z4, z4 = acc + b4 (no bias in linear mode), written in TG.
+template <typename TU, typename TG>
+__global__ void __launch_bounds__(256)
+net_out_mma(const bf16 *__restrict__ a3, int m, const bf16 *__restrict__ B4, const float *__restrict__ b4,
+            const TU *__restrict__ u, int sx, int sy, int sz, TG *__restrict__ g_out, int lin)
+{
+    extern __shared__ uint4 sm_om[];
+    uint4 *act = sm_om;                // 2000 chunks
+    uint4 *bs = sm_om + 2000;          // 432 chunks: [27][8 n][2]
+    const int s = blockIdx.y;
+    const long long P = (long long)m * m * m;
+    const Tile T = tile_of(blockIdx.x, m);
+    load_halo16(act, a3 + 16 * s * P, T, m);
+    for (int i = threadIdx.x; i < 432; i += blockDim.x) bs[i] = reinterpret_cast<const uint4 *>(B4)[i];
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+    const int arow = (lane & 7) + ((lane >> 3) & 1) * 8;
+    const int akh = lane >> 4;
+    const int bh = (lane >> 3) & 1, br = lane & 7;
+    for (int t = 0; t < 27; ++t) {
+        const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+        unsigned b[2];
+        ldsm_x2(smem_u32(bs + (t * 8 + br) * 2 + bh), b);
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt) {
+            const int x = arow & 7, y = 2 * mt + (arow >> 3), z = w;
+            const int q = ((z + 1 + dz) * 10 + (y + 1 + dy)) * 10 + (x + 1 + dx);
+            unsigned a[4];
+            ldsm_x4(smem_u32(act + chunk(q, akh)), a);
+            mma_bf16(acc[mt], a, b[0], b[1]);
+        }
+    }
+    // output channel 0 sits in column 0 of the accumulator: lanes with tq == 0
+    const int g = lane >> 2, tq = lane & 3;
+    if (tq != 0) return;
+    const float bias = lin ? 0.f : b4[0];
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int row = g + 8 * hh;
+            const int x = row & 7, y = 2 * mt + (row >> 3), z = w;
+            const int gx = T.ox + x, gy = T.oy + y, gz = T.oz + z;
+            const long long p = ((long long)gz * m + gy) * m + gx;
+            const long long ps = ((long long)wrap(gz - sz + m, m) * m + wrap(gy - sy + m, m)) * m +
+                                 wrap(gx - sx + m, m);
+            const float z4 = acc[mt][2 * hh] + bias;
+            g_out[s * P + p] = (TG)((double)u[s * P + ps] + (double)z4);
+        }
+}
 
 // g = S(u) + z4, z4 = conv(a3, W4) + b4.  With a target: r = g - tgt,
 // dz4 = bf16(r * grad_scale), loss partial sum r^2 per block.
@@ -562,11 +650,17 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
 // Operand copies from the FP32 masters (layout of NetLayout).
 __global__ void prepare_operands(const float *__restrict__ master, float *__restrict__ W1q,
                                  bf16 *__restrict__ B2f, bf16 *__restrict__ B3f,
-                                 bf16 *__restrict__ B2b, bf16 *__restrict__ B3b, float *__restrict__ W4q)
+                                 bf16 *__restrict__ B2b, bf16 *__restrict__ B3b, float *__restrict__ W4q,
+                                 bf16 *__restrict__ B4f)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < 864) W1q[j] = bf16r(master[NET_W1 + j]);
     if (j < 432) W4q[j] = bf16r(master[NET_W4 + j]);
+    if (j < 27 * 8 * 16) {
+        // last-layer operand [tap][n][k = ci]: row n = 0 holds W4[ci][tap], rows 1-7 zero
+        const int k = j % 16, n = (j / 16) % 8, tap = j / 128;
+        B4f[j] = __float2bfloat16_rn(n == 0 ? master[NET_W4 + k * 27 + tap] : 0.f);
+    }
     if (j < 6912) {
         // j = (co * 16 + ci) * 27 + tap  (master order)
         const int tap = j % 27, ci = (j / 27) % 16, co = j / (27 * 16);
@@ -590,7 +684,7 @@ cudaError_t launch_net_in_fwd(const TU *u, int m, const int s[3], const float *n
                               const float *W1q, const float *b1, float *z1, bf16 *a1, cudaStream_t st,
                               int lin)
 {
-    net_in_fwd<TU><<<dim3(tiles_of(m), batch), 512, 0, st>>>(u, m, s[0], s[1], s[2], nu_hat, W1q, b1, z1, a1,
+    net_in_fwd<TU><<<dim3(tiles_of(m), batch), 128, 0, st>>>(u, m, s[0], s[1], s[2], nu_hat, W1q, b1, z1, a1,
                                                              lin);
     return cudaGetLastError();
 }
@@ -712,11 +806,31 @@ cudaError_t launch_adam(float *p, const float *g, float *mo, float *vo, int L, f
 }
 
 cudaError_t launch_prepare_operands(const float *master, float *W1q, bf16 *B2f, bf16 *B3f, bf16 *B2b,
-                                    bf16 *B3b, float *W4q, cudaStream_t st)
+                                    bf16 *B3b, float *W4q, bf16 *B4f, cudaStream_t st)
 {
-    prepare_operands<<<(6912 + 255) / 256, 256, 0, st>>>(master, W1q, B2f, B3f, B2b, B3b, W4q);
+    prepare_operands<<<(6912 + 255) / 256, 256, 0, st>>>(master, W1q, B2f, B3f, B2b, B3b, W4q, B4f);
     return cudaGetLastError();
 }
+
+static constexpr size_t OM_SMEM = (2000 + 432) * 16;
+
+template <typename TU, typename TG>
+cudaError_t launch_net_out_mma(const bf16 *a3, int m, int batch, const bf16 *B4f, const float *b4,
+                               const TU *u, const int s[3], TG *g_out, cudaStream_t st, int lin)
+{
+    net_out_mma<TU, TG><<<dim3(tiles_of(m), batch), 256, OM_SMEM, st>>>(a3, m, B4f, b4, u, s[0], s[1],
+                                                                       s[2], g_out, lin);
+    return cudaGetLastError();
+}
+template cudaError_t launch_net_out_mma<float, float>(const bf16 *, int, int, const bf16 *, const float *,
+                                                      const float *, const int *, float *, cudaStream_t, int);
+template cudaError_t launch_net_out_mma<double, double>(const bf16 *, int, int, const bf16 *, const float *,
+                                                        const double *, const int *, double *, cudaStream_t,
+                                                        int);
+template cudaError_t launch_net_out_mma<float, double>(const bf16 *, int, int, const bf16 *, const float *,
+                                                       const float *, const int *, double *, cudaStream_t, int);
+template cudaError_t launch_net_out_mma<double, float>(const bf16 *, int, int, const bf16 *, const float *,
+                                                       const double *, const int *, float *, cudaStream_t, int);
 
 }  // namespace pr
 

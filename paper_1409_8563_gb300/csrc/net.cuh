@@ -17,6 +17,14 @@ constexpr int NET_OUT_PARTIAL = 433;             // dW4[16][27] + db4
 constexpr int NET_IN_PARTIAL = 880;              // dW1[16][2][27] + db1[16]
 
 cudaError_t configure_net_kernels();
+// 16 -> 16 forward layer on the 5th-generation tensor cores (net_tc.cu);
+// m a multiple of 16.  errflag (device int) is set if an MMA completion wait
+// runs out.
+cudaError_t configure_net_tc();
+bool net_tc_supported(int m);
+cudaError_t launch_net_mid_tc(const __nv_bfloat16 *in, int m, int batch, const __nv_bfloat16 *Bt,
+                              const float *bias, __nv_bfloat16 *out, int lin, int *errflag,
+                              cudaStream_t st);
 template <typename TU>
 cudaError_t launch_net_in_fwd(const TU *u, int m, const int s[3], const float *nu_hat, int batch,
                               const float *W1q, const float *b1, float *z1, __nv_bfloat16 *a1,
@@ -48,6 +56,11 @@ cudaError_t launch_adam(float *p, const float *g, float *mo, float *vo, int L, f
                         float b2, float eps, float c1, float c2, cudaStream_t st);
 cudaError_t launch_prepare_operands(const float *master, float *W1q, __nv_bfloat16 *B2f,
                                     __nv_bfloat16 *B3f, __nv_bfloat16 *B2b, __nv_bfloat16 *B3b,
-                                    float *W4q, cudaStream_t st);
+                                    float *W4q, __nv_bfloat16 *B4f, cudaStream_t st);
+// Last layer for inference on the tensor cores (B4f: [27][8][16], row 0 = W4).
+template <typename TU, typename TG>
+cudaError_t launch_net_out_mma(const __nv_bfloat16 *a3, int m, int batch, const __nv_bfloat16 *B4f,
+                               const float *b4, const TU *u, const int s[3], TG *g_out,
+                               cudaStream_t st, int lin = 0);
 
 }  // namespace pr
