@@ -93,17 +93,23 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Load the 10^3 halo of a [P][16] BF16 field (swizzled chunks) into smem.
+// Load the 10^3 halo of a [P][16] BF16 field (swizzled chunks) into smem:
+// 16-byte asynchronous copies, all in flight before the thread waits for its
+// own (the caller's barrier then publishes them to the block).
 __device__ __forceinline__ void load_halo16(uint4 *sm, const bf16 *__restrict__ in, const Tile &T,
                                             int m)
 {
+    const uint4 *src = reinterpret_cast<const uint4 *>(in);
     for (int i = threadIdx.x; i < 2000; i += blockDim.x) {
         const int q = i >> 1, h = i & 1;
         const int hx = q % 10, hy = (q / 10) % 10, hz = q / 100;
         const int gx = wrap(T.ox + hx - 1, m), gy = wrap(T.oy + hy - 1, m), gz = wrap(T.oz + hz - 1, m);
         const long long p = ((long long)gz * m + gy) * m + gx;
-        sm[chunk(q, h)] = reinterpret_cast<const uint4 *>(in)[2 * p + h];
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n"
+                     ::"r"((unsigned)__cvta_generic_to_shared(sm + chunk(q, h))), "l"(src + 2 * p + h)
+                     : "memory");
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 // ---------------------------------------------------------------- layer 1

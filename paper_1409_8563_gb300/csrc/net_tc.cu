@@ -3,11 +3,11 @@
 // accumulator in tensor memory.
 //
 // One MMA computes D[128 x 16] += A[128 x 16] * B[16 x 16] (BF16 in, FP32
-// accumulate).  An output tile is 8 x 16 x 1 points (M = 128, row m = x + 8 y);
-// the layer is 27 MMAs, one per tap, each with K = 16 input channels:
+// accumulate).  An output plane tile is 8 x 16 points (M = 128, row m = x + 8 y);
+// it is 27 MMAs, one per tap, each with K = 16 input channels:
 //   D[m][co] = sum_tap sum_ci act[p(m) + tap][ci] * W[tap][co][ci].
-// The 27 A operands are not copied: the activations of the tile's halo
-// (10 x 18 x 3 points) sit in shared memory in the layout
+// The A operands are not copied: the activations of the tile's halo (10 x 18
+// x (ZB + 2) points for ZB output planes) sit in shared memory in the layout
 //   chunk(z, y, h, x) = ((z * 18 + y) * 2 + h) * 10 + x     (16-byte chunks,
 //   h = channel half),
 // so the 8 points x .. x+7 of one halo row and channel half form one 8 x 16 B
@@ -16,11 +16,12 @@
 // groups (y) 320 B, between the two channel halves 160 B (K-major, no
 // swizzle).  B (the tap's 16 x 16 weights) is stored [tap][h][co] the same way.
 //
-// Each CTA (4 warps) allocates 32 tensor-memory columns once, loops over
-// tiles, and reads D back with tcgen05.ld (warp w owns lanes 32w .. 32w+31,
-// i.e. tile rows 32w .. 32w+31).  Completion of the MMAs is signalled on an
-// mbarrier whose wait is bounded: on timeout the kernel records an error flag,
-// waits once more (bounded), frees its tensor memory and returns.
+// Each CTA (4 warps) allocates 32 tensor-memory columns once (one 16-column
+// accumulator per output plane), loops over tiles, and reads D back with
+// tcgen05.ld (warp w owns lanes 32w .. 32w+31, i.e. tile rows 32w .. 32w+31).
+// Completion of the MMAs is signalled on an mbarrier whose wait is bounded: on
+// timeout the kernel records an error flag, waits once more (bounded), frees
+// its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -33,12 +34,13 @@ using bf16 = __nv_bfloat16;
 
 namespace {
 
-constexpr int HX = 10, HY = 18, HZ = 3;
-constexpr int HALO_CHUNKS = HZ * HY * 2 * HX;     // 1080 chunks, 17280 B
-constexpr int HALO_ALLOC = HALO_CHUNKS + 256;     // slack past the last chunk any operand reads
+constexpr int ZB = 2;                             // output planes per tile (one accumulator each)
+constexpr int HX = 10, HY = 18, HZ = ZB + 2;
+constexpr int HALO_CHUNKS = HZ * HY * 2 * HX;     // 1440 chunks, 23040 B
+constexpr int HALO_ALLOC = HALO_CHUNKS + 32;      // per buffer, 16-byte chunks
 constexpr int B_CHUNKS = 27 * 2 * 16;             // 864 chunks, 13824 B
 constexpr int TC_THREADS = 128;
-constexpr uint32_t TMEM_COLS = 32;
+constexpr uint32_t TMEM_COLS = 32;                // ZB accumulators of 16 columns
 constexpr long long WAIT_LIMIT = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -98,6 +100,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
     return false;
 }
 
+__device__ __forceinline__ void cp_async16_tc(uint32_t saddr, const void *g)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(g) : "memory");
+}
+
 __device__ __forceinline__ float gelu_tc(float x)
 {
     return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
@@ -105,26 +112,57 @@ __device__ __forceinline__ float gelu_tc(float x)
 
 __device__ __forceinline__ int wrapi(int i, int m) { return i < 0 ? i + m : (i >= m ? i - m : i); }
 
+struct TileTC {
+    int s, ox, oy, oz;
+};
+__device__ __forceinline__ TileTC tile_tc(long long tt, int m)
+{
+    const int tx_n = m / 8, ty_n = m / 16, tz_n = m / ZB;
+    const long long per = (long long)tx_n * ty_n * tz_n;
+    TileTC T;
+    T.s = (int)(tt / per);
+    const long long r = tt % per;
+    T.ox = (int)(r % tx_n) * 8;
+    T.oy = (int)((r / tx_n) % ty_n) * 16;
+    T.oz = (int)(r / ((long long)tx_n * ty_n)) * ZB;
+    return T;
+}
+
+// Queue the halo of tile T into the buffer at shared address `buf`
+// (chunk(z, y, h, x) = ((z * HY + y) * 2 + h) * HX + x; 16-byte copies).
+__device__ __forceinline__ void halo_async(uint32_t buf, const bf16 *__restrict__ in, const TileTC &T,
+                                           int m, long long P)
+{
+    const uint4 *src = reinterpret_cast<const uint4 *>(in + 16 * T.s * P);
+    for (int i = threadIdx.x; i < HALO_CHUNKS; i += TC_THREADS) {
+        const int x = i % HX, h = (i / HX) & 1, y = (i / (2 * HX)) % HY, z = i / (2 * HX * HY);
+        const int gx = wrapi(T.ox + x - 1, m), gy = wrapi(T.oy + y - 1, m), gz = wrapi(T.oz + z - 1, m);
+        cp_async16_tc(buf + (uint32_t)i * 16u, src + 2 * (((long long)gz * m + gy) * m + gx) + h);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
 }  // namespace
 
 // out[p][co] = bf16(act(sum_tap sum_ci in[p + tap][ci] W[tap][co][ci] + bias[co]))
 // (linear mode: no bias, identity).  Bt: [tap][co][ci] BF16 (the forward operand
-// of net_mid).  Tiles: per sample (m/8) x (m/16) x m; m must be a multiple of 16.
+// of net_mid).  A tile is 8 x 16 x ZB points: ZB GEMMs of M = 128 on one halo,
+// accumulators at columns 16 zp .. 16 zp + 15.  Persistent CTAs: the halo of
+// the next tile streams in (cp.async, double buffer) while the current tile's
+// MMAs and epilogue run.  m must be a multiple of 16.
 __global__ void __launch_bounds__(TC_THREADS)
 net_mid_tc(const bf16 *__restrict__ in, int m, int batch, const bf16 *__restrict__ Bt,
            const float *__restrict__ bias, bf16 *__restrict__ out, int lin, int *__restrict__ errflag)
 {
     extern __shared__ __align__(1024) uint4 sm_tc[];
-    uint4 *halo = sm_tc;
-    uint4 *bs = sm_tc + HALO_ALLOC;
+    uint4 *halo0 = sm_tc;
+    uint4 *bs = sm_tc + 2 * HALO_ALLOC;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long P = (long long)m * m * m;
-    const int tx_n = m / 8, ty_n = m / 16;
-    const long long tiles_per = (long long)tx_n * ty_n * m;
-    const long long tiles = tiles_per * batch;
+    const long long tiles = (long long)(m / 8) * (m / 16) * (m / ZB) * batch;
 
     // B: [tap][co][ci] (two chunks per co row) -> [tap][h][co]
     const uint4 *bsrc = reinterpret_cast<const uint4 *>(Bt);
@@ -141,75 +179,85 @@ net_mid_tc(const bf16 *__restrict__ in, int m, int batch, const bf16 *__restrict
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar)));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
     }
+    const uint32_t halo_a[2] = {smem_addr(halo0), smem_addr(halo0 + HALO_ALLOC)};
+    long long tt = blockIdx.x;
+    if (tt < tiles) halo_async(halo_a[0], in, tile_tc(tt, m), m, P);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     const uint32_t tmem = tmem_slot;
     const uint32_t mbar_a = smem_addr(&mbar);
-    const uint32_t halo_a = smem_addr(halo), bs_a = smem_addr(bs);
+    const uint32_t bs_a = smem_addr(bs);
     constexpr uint32_t IDESC = idesc_bf16(128, 16);
 
     uint32_t parity = 0;
-    bool ok = true;
-    for (long long tt = blockIdx.x; tt < tiles && ok; tt += gridDim.x) {
-        const int s = (int)(tt / tiles_per);
-        const long long r = tt % tiles_per;
-        const int ox = (int)(r % tx_n) * 8, oy = (int)((r / tx_n) % ty_n) * 16, oz = (int)(r / ((long long)tx_n * ty_n));
-        const uint4 *src = reinterpret_cast<const uint4 *>(in + 16 * s * P);
-        for (int i = tid; i < HALO_CHUNKS; i += TC_THREADS) {
-            const int x = i % HX, h = (i / HX) & 1, y = (i / (2 * HX)) % HY, z = i / (2 * HX * HY);
-            const int gx = wrapi(ox + x - 1, m), gy = wrapi(oy + y - 1, m), gz = wrapi(oz + z - 1, m);
-            halo[i] = src[2 * (((long long)gz * m + gy) * m + gx) + h];
-        }
-        // generic-proxy shared stores -> visible to the tensor core's async proxy
+    int buf = 0;
+    for (; tt < tiles; tt += gridDim.x, buf ^= 1) {
+        const TileTC T = tile_tc(tt, m);
+        // the next tile's halo goes to the other buffer, whose last reader
+        // (the previous tile's MMAs) has completed
+        const long long nt = tt + gridDim.x;
+        if (nt < tiles) halo_async(halo_a[buf ^ 1], in, tile_tc(nt, m), m, P);
+        else asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        // this thread's copies -> visible to the tensor core's async proxy
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
         if (tid == 0) {
-            for (int t = 0; t < 27; ++t) {
-                const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;     // offsets + 1
-                const uint32_t a_off = (uint32_t)(((dz * HY + dy) * 2) * HX + dx) * 16u;
-                const uint64_t ad = smem_desc(halo_a + a_off, HX * 16, 2 * HX * 16);
-                const uint64_t bd = smem_desc(bs_a + (uint32_t)t * 512u, 256, 128);
-                mma_tc(tmem, ad, bd, IDESC, t > 0 ? 1u : 0u);
-            }
+            // descriptors of the halo and weight bases; each tap adds its offset
+            // (in 16-byte units) to the start-address field, which stays below
+            // 2^14 for any shared-memory address
+            const uint64_t a0 = smem_desc(halo_a[buf], HX * 16, 2 * HX * 16);
+            const uint64_t b0 = smem_desc(bs_a, 256, 128);
+#pragma unroll
+            for (int zp = 0; zp < ZB; ++zp)
+#pragma unroll
+                for (int t = 0; t < 27; ++t) {
+                    const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;     // offsets + 1
+                    const uint32_t a_chunk = (uint32_t)((((zp + dz) * HY + dy) * 2) * HX + dx);
+                    mma_tc(tmem + 16u * zp, a0 + a_chunk, b0 + (uint64_t)(t * 32), IDESC, t > 0 ? 1u : 0u);
+                }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
                          ::"r"(mbar_a) : "memory");
         }
         if (!mbar_wait_bounded(mbar_a, parity)) {
             if (tid == 0) atomicExch(errflag, 1);
             mbar_wait_bounded(mbar_a, parity);
-            ok = false;
             break;
         }
         parity ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-        uint32_t v[16];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-              "=r"(v[14]), "=r"(v[15])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
         const int row = warp * 32 + lane;
-        const long long p = s * P + ((long long)oz * m + (oy + (row >> 3))) * m + ox + (row & 7);
-        __align__(16) bf16 o[16];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-            float x = __uint_as_float(v[c]);
-            if (!lin) x = gelu_tc(x + bias[c]);
-            o[c] = __float2bfloat16_rn(x);
+        for (int zp = 0; zp < ZB; ++zp) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + 16u * zp;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                  "=r"(v[14]), "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            const long long p = T.s * P + ((long long)(T.oz + zp) * m + (T.oy + (row >> 3))) * m + T.ox + (row & 7);
+            __align__(16) bf16 o[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                float x = __uint_as_float(v[c]);
+                if (!lin) x = gelu_tc(x + bias[c]);
+                o[c] = __float2bfloat16_rn(x);
+            }
+            uint4 *op = reinterpret_cast<uint4 *>(out + 16 * p);
+            op[0] = reinterpret_cast<const uint4 *>(o)[0];
+            op[1] = reinterpret_cast<const uint4 *>(o)[1];
         }
-        uint4 *op = reinterpret_cast<uint4 *>(out + 16 * p);
-        op[0] = reinterpret_cast<const uint4 *>(o)[0];
-        op[1] = reinterpret_cast<const uint4 *>(o)[1];
         // every warp's tensor-memory reads precede the next tile's MMAs
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
@@ -217,7 +265,7 @@ net_mid_tc(const bf16 *__restrict__ in, int m, int batch, const bf16 *__restrict
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
-static constexpr size_t TC_SMEM = (size_t)(HALO_ALLOC + B_CHUNKS) * 16;
+static constexpr size_t TC_SMEM = (size_t)(2 * HALO_ALLOC + B_CHUNKS) * 16;
 
 cudaError_t configure_net_tc()
 {
@@ -229,8 +277,8 @@ bool net_tc_supported(int m) { return m >= 16 && m % 16 == 0; }
 cudaError_t launch_net_mid_tc(const bf16 *in, int m, int batch, const bf16 *Bt, const float *bias,
                               bf16 *out, int lin, int *errflag, cudaStream_t st)
 {
-    const long long tiles = (long long)(m / 8) * (m / 16) * m * batch;
-    const long long cap = 152 * 6;
+    const long long tiles = (long long)(m / 8) * (m / 16) * (m / ZB) * batch;
+    const long long cap = 152 * 3;      // three CTAs of 60 KB shared memory per SM
     const int grid = (int)(tiles < cap ? tiles : cap);
     net_mid_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(in, m, batch, Bt, bias, out, lin, errflag);
     return cudaGetLastError();
