@@ -212,6 +212,10 @@ def run(args):
         cfg, u0 = configs.fp32_256(seed=rank)
         desc = ("fp32_256: Parareal to d^k <= 1e-6, 256^3, N=32, dt_F=1/8192, "
                 "coarse RK4 on 32^3 at 1/256, k^-2 field to k=32")
+    # the stencil G is linear: Eq. (parareal) evaluated as F(U^k[n]) + G(U^{k+1}[n] - U^k[n])
+    # (the same iteration, with G's FP32 rounding scaled by the change of its input)
+    cfg.correction_form = (native.CORRECTION_DIFFERENCE if args.correction == "difference"
+                           else native.CORRECTION_STANDARD)
     n, N = cfg.n, cfg.n_slices
     P = n ** 3
     nf = round(cfg.T / N / cfg.dt_fine)
@@ -313,7 +317,7 @@ def run(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "precision": "FP32 stencil; FP64 correction, norms and nu(t)",
         "data": "synthetic",
-        "config": {"workload": desc,
+        "config": {"workload": desc, "correction_form": args.correction,
                    "n": n, "n_slices": N, "fine_steps_per_slice": nf,
                    "l2": ("inputs larger than L2 (%.2f GB per field set)" % (4.0 * N * P / 1e9)),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -524,6 +528,8 @@ def run_batch64(args):
     cfgs, u0s = [], []
     for i, (n, nu0) in enumerate(zip(ns, nus)):
         cfg, u0 = configs.batch_instance(n, nu0, seed=i)
+        cfg.correction_form = (native.CORRECTION_DIFFERENCE if args.correction == "difference"
+                               else native.CORRECTION_STANDARD)
         cfgs.append(cfg)
         u0s.append(torch.from_numpy(u0).cuda())
     b = native.Batch(cfgs)
@@ -546,6 +552,7 @@ def run_batch64(args):
     print(json.dumps({"workload": "batch64", "time_to_1e-6_ms": ms, "serial_fine_ms": serial_ms,
                       "k_star": [int(x) for x in k], "max_defect": float(max(d)),
                       "glups_in_solve": ups / ms / 1e6, "autotune_ms": tune_ms,
+                      "correction_form": args.correction,
                       "graph_launches": b.graph_launches()}))
     b.close()
     return 0
@@ -597,6 +604,8 @@ def main():
                     choices=["fp32_256", "fp32_128", "fp64_32", "learned_128", "batch64",
                              "fine_sweep", "paper_faithful"])
     ap.add_argument("--slices", type=int, default=8)
+    ap.add_argument("--correction", default="difference", choices=["difference", "standard"],
+                    help="evaluation of the Parareal correction (fp32_256 / fp32_128 / batch64)")
     ap.add_argument("--tile", default=None, help="fine_sweep: fused tile 'tx,ty,zchunk' instead of autotuning")
     ap.add_argument("--n-ics", type=int, default=63)
     ap.add_argument("--epochs", type=int, default=10)
