@@ -33,7 +33,9 @@ sys.path.insert(0, ROOT)
 METRIC = ("time-to-1e-6-error Parareal vs serial fine on 1 GB300; stencil GLUP/s, % HBM peak")
 UNIT = "GLUP/s"
 TOL = 1e-6
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "rk4_fused_256.md")
+# ncu summary and kernel source of the batched fine sweep, per launch path
+PROFILE_SUMMARY = {0: (os.path.join(ROOT, "profiles", "rk4_fused_256.md"), "stencil.cu"),
+                   2: (os.path.join(ROOT, "profiles", "rk4_fused_rows2_256.md"), "stencil.cu")}
 TUNE_CACHE = os.path.join(ROOT, "paper_1409_8563_gb300", "tune_cache.jsonl")
 
 
@@ -46,22 +48,24 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def stencil_hash():
+def stencil_hash(src="stencil.cu"):
     h = hashlib.sha1()
-    with open(os.path.join(ROOT, "paper_1409_8563_gb300", "csrc", "stencil.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_1409_8563_gb300", "csrc", src), "rb") as f:
         h.update(f.read())
     return h.hexdigest()[:12]
 
 
-def ncu_traffic():
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
-    or None when the summary is missing or the kernel source changed since."""
-    if not os.path.exists(PROFILE_SUMMARY):
+def ncu_traffic(path):
+    """DRAM bytes per launch of the fine-sweep kernel of launch path `path`
+    from the committed ncu summary, or None when the summary is missing or the
+    kernel source changed since."""
+    if path not in PROFILE_SUMMARY or not os.path.exists(PROFILE_SUMMARY[path][0]):
         return None
-    text = open(PROFILE_SUMMARY).read()
+    summary, src = PROFILE_SUMMARY[path]
+    text = open(summary).read()
     m = re.search(r"stencil_sha1:\s*([0-9a-f]+)", text)
     t = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
-    if not m or not t or m.group(1) != stencil_hash():
+    if not m or not t or m.group(1) != stencil_hash(src):
         return None
     return float(t.group(1))
 
@@ -224,8 +228,9 @@ def run(args):
     # launch shapes from the autotuner (cached per grid, dtype, batch and SM count)
     ctx.autotune(TUNE_CACHE)
     fine_shape, coarse_shape, serial_shape = ctx.launch_shape()
-    kernel = (f"rk4_fused_kernel<float,{fine_shape[1]},{fine_shape[2]}> zchunk {fine_shape[3]}"
-              if fine_shape[0] == 0 else "rk4_stage_kernel<float>")
+    kernel = {0: f"rk4_fused_kernel<float,{fine_shape[1]},{fine_shape[2]},1> zchunk {fine_shape[3]}",
+              2: f"rk4_fused_kernel<float,{fine_shape[1]},{fine_shape[2]},2> zchunk {fine_shape[3]}"}.get(
+                  fine_shape[0], "rk4_stage_kernel<float>")
     u0_dev = torch.from_numpy(u0).to("cuda")
     u0_host = torch.from_numpy(u0).pin_memory()
     out_host = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
@@ -297,7 +302,7 @@ def run(args):
     avg_launch_ms = fine_ms / max(fine_launches, 1)
     bytes_per_launch = fine_bytes / max(fine_launches, 1)
     achieved = bytes_per_launch / (avg_launch_ms / 1000.0) / 1e9
-    traffic = ncu_traffic() if args.workload == "fp32_256" else None
+    traffic = ncu_traffic(fine_shape[0]) if args.workload == "fp32_256" else None
     k_star = max(len(h) for h in hists)
     final_defect = float(hists[-1][-1, 2])
 
@@ -320,7 +325,9 @@ def run(args):
         "config": {"workload": desc, "correction_form": args.correction,
                    "n": n, "n_slices": N, "fine_steps_per_slice": nf,
                    "l2": ("inputs larger than L2 (%.2f GB per field set)" % (4.0 * N * P / 1e9)),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "launch_shapes": {"fine_sweep": list(fine_shape), "coarse": list(coarse_shape),
+                                     "serial_fine": list(serial_shape)}},
         "time_to_1e-6_ms": total_ms / args.steps,
         "serial_fine_ms": serial_ms,
         "parareal_over_serial": (total_ms / args.steps) / serial_ms,
@@ -568,7 +575,9 @@ def run_fine_sweep(args):
     n, S, steps = 256, args.slices, 4
     cfg = native.Config.make(n, S, S * steps / 8192, 1 / 8192, steps / 8192, 8, fine_dtype=native.F32)
     if args.tile:
-        os.environ["PARAREAL_FINE_TILE"] = "0," + args.tile
+        # "tx,ty,zchunk" (fused kernel, one row per thread) or "path,tx,ty,zchunk"
+        t = args.tile.split(",")
+        os.environ["PARAREAL_FINE_TILE"] = ",".join(t if len(t) == 4 else ["0"] + t)
     ctx = native.Parareal(cfg)
     if not args.tile:
         ctx.autotune(TUNE_CACHE)
@@ -606,7 +615,10 @@ def main():
     ap.add_argument("--slices", type=int, default=8)
     ap.add_argument("--correction", default="difference", choices=["difference", "standard"],
                     help="evaluation of the Parareal correction (fp32_256 / fp32_128 / batch64)")
-    ap.add_argument("--tile", default=None, help="fine_sweep: fused tile 'tx,ty,zchunk' instead of autotuning")
+    ap.add_argument("--tile", default=None,
+                    help="fine_sweep: launch shape 'tx,ty,zchunk' (fused kernel, one row per "
+                         "thread) or 'path,tx,ty,zchunk' (path 2: two rows per thread) instead of "
+                         "autotuning")
     ap.add_argument("--n-ics", type=int, default=63)
     ap.add_argument("--epochs", type=int, default=10)
     ap.add_argument("--batch", type=int, default=8)

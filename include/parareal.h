@@ -265,7 +265,8 @@ parareal_status parareal_coarse_model_grad(parareal_ctx *ctx, const float *u, co
                                            double *loss);
 
 /* Autotuner: times every compiled launch shape of the fine step kernel (tile
- * in x and y, z-march chunk, or the per-stage path) on this context's batch
+ * in x and y, one or two region rows per thread, z-march chunk, or the
+ * per-stage path) on this context's batch
  * of slices and on a single field, and of the coarse step kernel on the
  * coarse grid, keeps the fastest of each, and appends them to `cache_path`
  * (JSON lines keyed by grid edge,
@@ -275,8 +276,9 @@ parareal_status parareal_coarse_model_grad(parareal_ctx *ctx, const float *u, co
  * (-1 when taken from the cache). */
 parareal_status parareal_autotune(parareal_ctx *ctx, const char *cache_path, double *ms2);
 
-/* The launch shapes in use, each {path (0 fused, 1 per-stage), tile_x,
- * tile_y, z chunk}: the batched fine sweep, the coarse steps, and one fine
+/* The launch shapes in use, each {path (0 fused with one region row per
+ * thread, 1 per-stage, 2 fused with two rows per thread), tile_x, tile_y,
+ * z chunk}: the batched fine sweep, the coarse steps, and one fine
  * field at a time (serial fine run, propagate).  Any pointer may be NULL. */
 parareal_status parareal_get_launch_shape(const parareal_ctx *ctx, int *fine4, int *coarse4,
                                           int *serial4);

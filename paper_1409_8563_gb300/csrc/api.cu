@@ -163,10 +163,10 @@ static void default_tiles(int dtype, int n, int count, int *path, int *tx, int *
     *tx = *ty = 0;
     if (dtype == PARAREAL_F32) {
         for (auto &t : cand)
-            if (rk4_fused_supported(dtype, n, t[0], t[1])) { *tx = t[0]; *ty = t[1]; break; }
+            if (rk4_fused_supported(dtype, n, t[0], t[1], 1)) { *tx = t[0]; *ty = t[1]; break; }
     } else {
         for (auto &t : candd)
-            if (rk4_fused_supported(dtype, n, t[0], t[1])) { *tx = t[0]; *ty = t[1]; break; }
+            if (rk4_fused_supported(dtype, n, t[0], t[1], 1)) { *tx = t[0]; *ty = t[1]; break; }
     }
     if (*tx == 0) { *path = PATH_STAGED; *tx = 16; *ty = 8; }
     // z chunk: whole columns unless the launch would leave SMs idle
@@ -181,8 +181,8 @@ static bool tile_override(const char *var, int dtype, int n, int *path, int *tx,
     if (!e || !*e) return true;
     int p, x, y, z;
     if (std::sscanf(e, "%d,%d,%d,%d", &p, &x, &y, &z) != 4) return false;
-    if (p != PATH_FUSED && p != PATH_STAGED) return false;
-    if (p == PATH_FUSED && (!rk4_fused_supported(dtype, n, x, y) || z < 1)) return false;
+    if (!is_fused(p) && p != PATH_STAGED) return false;
+    if (is_fused(p) && (!rk4_fused_supported(dtype, n, x, y, fused_rows(p)) || z < 1)) return false;
     *path = p; *tx = x; *ty = y; *zc = z;
     return true;
 }
@@ -205,7 +205,7 @@ parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, int first
                           long long nsteps, double dt, int path, int tx, int ty, int zc, T *ws1,
                           T *ws2, T *ws3, int slice_stride, int op)
 {
-    if (path == PATH_FUSED && op != OP_C2)
+    if (is_fused(path) && op != OP_C2)
         return fail(c, PARAREAL_E_INVALID, "the fused RK4 kernel implements the 7-point operator only");
     StepArgs a{};
     a.op = op;
@@ -221,7 +221,7 @@ parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, int first
     a.nu_amp = c->cfg.nu_amp;
     a.nu_omega = c->cfg.nu_omega;
     a.frozen = c->cfg.nu_mode == PARAREAL_NU_FROZEN;
-    if (path == PATH_FUSED) {
+    if (is_fused(path)) {
         const T *src = in;
         const bool timed = c->prof && m == c->n;
         for (long long j = 0; j < nsteps; ++j) {
@@ -231,7 +231,7 @@ parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, int first
                 parareal_status ps = prof_begin(c);
                 if (ps != PARAREAL_OK) return ps;
             }
-            LK((launch_rk4_fused<T>(a, src, dst, tx, ty, zc, c->st)));
+            LK((launch_rk4_fused<T>(a, src, dst, tx, ty, zc, fused_rows(path), c->st)));
             if (timed) {
                 CK(cudaEventRecord(c->ev_pool[c->ev_used - 1], c->st));
                 c->prof_bytes += 2.0 * (double)count * (double)a.P * sizeof(T);
@@ -321,7 +321,7 @@ static parareal_status fine_sweep_t(parareal_ctx *c, int first, int count)
     }
     // the fused path must not read and write the same buffer
     T *ws1 = static_cast<T *>(c->wA), *ws2 = static_cast<T *>(c->wB), *ws3 = static_cast<T *>(c->wC);
-    if (c->fine_path == PATH_FUSED && in == ws1) std::swap(ws1, ws3);
+    if (is_fused(c->fine_path) && in == ws1) std::swap(ws1, ws3);
     return rk4_batch<T>(c, c->n, in, Fv, first, count, c->Nf, c->cfg.dt_fine, c->fine_path,
                         c->fine_tx, c->fine_ty, c->fine_zc, ws1, ws2, ws3, 1, c->fine_op);
 }
@@ -1032,18 +1032,19 @@ static parareal_status time_shape(parareal_ctx *c, int m, int count, int path, i
     return s;
 }
 
-// Candidates: every compiled fused shape that divides m, whole-column and
-// chunked z marches, and the per-stage path.
+// Candidates: every compiled fused shape (one and two rows per thread) that
+// divides m, whole-column and chunked z marches, and the per-stage path.
 static void candidates(int dtype, int m, std::vector<std::array<int, 4>> *out)
 {
-    const int shapes[][2] = {{64, 32}, {64, 16}, {64, 8}, {32, 16}, {32, 8}, {16, 16}, {16, 8}};
-    for (auto &sh : shapes) {
-        if (!rk4_fused_supported(dtype, m, sh[0], sh[1])) continue;
-        for (int zc = m; zc >= 8; zc /= 2) {
-            out->push_back({PATH_FUSED, sh[0], sh[1], zc});
-            if (zc <= m / 8) break;
+    const int shapes[][2] = {{64, 32}, {64, 16}, {64, 8}, {32, 32}, {32, 16}, {32, 8}, {16, 16}, {16, 8}};
+    for (int path : {PATH_FUSED, PATH_FUSED2})
+        for (auto &sh : shapes) {
+            if (!rk4_fused_supported(dtype, m, sh[0], sh[1], fused_rows(path))) continue;
+            for (int zc = m; zc >= 8; zc /= 2) {
+                out->push_back({path, sh[0], sh[1], zc});
+                if (zc <= m / 8) break;
+            }
         }
-    }
     out->push_back({PATH_STAGED, 16, 8, m});
 }
 
@@ -1094,7 +1095,7 @@ static parareal_status tune_one(parareal_ctx *c, const char *cache, int m, int c
     const std::string key = tune_key(dtype, m, count);
     int sh[4];
     if (cache_lookup(cache, key, sh) &&
-        (sh[0] == PATH_STAGED || rk4_fused_supported(dtype, m, sh[1], sh[2]))) {
+        (sh[0] == PATH_STAGED || (is_fused(sh[0]) && rk4_fused_supported(dtype, m, sh[1], sh[2], fused_rows(sh[0]))))) {
         *path = sh[0]; *tx = sh[1]; *ty = sh[2]; *zc = sh[3];
         *best_ms = -1.0;
         return PARAREAL_OK;

@@ -9,7 +9,12 @@
 
 #include "internal.cuh"
 
-enum { PATH_FUSED = 0, PATH_STAGED = 1 };
+// Launch paths of an RK4 sweep: the fused kernel with one region row per
+// thread, the per-stage kernels, the fused kernel with two rows per thread.
+enum { PATH_FUSED = 0, PATH_STAGED = 1, PATH_FUSED2 = 2 };
+// region rows per thread of a fused launch path
+inline int fused_rows(int path) { return path == PATH_FUSED2 ? 2 : 1; }
+inline bool is_fused(int path) { return path == PATH_FUSED || path == PATH_FUSED2; }
 
 // Device state of the learned coarse propagator (allocated on demand).
 struct NetState {

@@ -90,11 +90,12 @@ __host__ __device__ inline void op_weights(int op, double nu, double dt, int n, 
 // ------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return cudaGetLastError().
 
-// Fused z-marching RK4 step (one full step per launch, all stages on chip).
+// Fused z-marching RK4 step (one full step per launch, all stages on chip);
+// `rows` = region rows per thread (1 or 2).
 template <typename T>
 cudaError_t launch_rk4_fused(const StepArgs &a, const T *in, T *out, int tile_x, int tile_y,
-                             int zchunk, cudaStream_t st);
-bool rk4_fused_supported(int dtype, int n, int tile_x, int tile_y);
+                             int zchunk, int rows, cudaStream_t st);
+bool rk4_fused_supported(int dtype, int n, int tile_x, int tile_y, int rows);
 cudaError_t configure_rk4_kernels();
 
 // One RK4 stage per launch (no halo recomputation; state kept in HBM/L2),

@@ -18,6 +18,9 @@
 //                     current plane sits in shared memory for its x/y
 //                     neighbours and its z neighbours sit in registers.  HBM
 //                     traffic: one read and one write of the field per step.
+//                     A thread owns a vector of points in R = 1 or 2 rows;
+//                     shared-memory traffic, not HBM, bounds the step, and
+//                     R = 2 cuts it by a quarter.
 //   rk4_stage_kernel  one stage per launch, one point per thread; no halo
 //                     recomputation, so the fewest arithmetic operations per
 //                     step (the right trade where FP64 throughput, not
@@ -84,23 +87,24 @@ __device__ __forceinline__ double nu_at(const StepArgs &a, double t)
     return a.nu0 * (1.0 + a.nu_amp * sin(a.nu_omega * t));
 }
 
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, int R>
 struct FusedShape {
     static constexpr int V = VecT<T>::V;
     static constexpr int RX = TX + 8;          // region width incl. 4-point halo per side
     static constexpr int RY = TY + 8;
     static constexpr int QX = RX / V;          // vectors per region row
-    static constexpr int NT = QX * RY;         // threads per CTA
+    static constexpr int NT = QX * RY / R;     // threads per CTA (R rows each)
     static constexpr int PL = RX * RY;         // values per shared plane
     static constexpr int EL = QX * RY;         // entries per edge array
     static constexpr int D = 4;                // planes of u in flight ahead of use
     static constexpr int RING = 6;             // u planes resident (divides the unroll of 12)
     // u ring [RING][PL], stage planes [2][3][PL], u edges [RING][2][EL], stage edges [2][3][2][EL]
     static constexpr size_t SMEM = ((size_t)(RING + 6) * PL + (size_t)(2 * RING + 12) * EL) * sizeof(T);
-    // CTAs per SM the register allocation is held to: as many as 64K
-    // registers allow at >= 128 registers per thread (latency hiding comes
-    // from independent CTAs: every CTA waits at a barrier once per plane)
-    static constexpr int MINB = NT * 2 * 128 <= 65536 ? 2 : 1;
+    // CTAs per SM the register allocation is held to: two where 64K
+    // registers still give every thread its working set (~128 registers at
+    // one row per thread, ~168 at two), else one (latency hiding comes from
+    // independent CTAs: every CTA waits at a barrier once per plane)
+    static constexpr int MINB = NT * 2 * (R == 1 ? 128 : 168) <= 65536 ? 2 : 1;
 };
 
 // 16-byte asynchronous global->shared copy (L2 only, bypassing L1) and its
@@ -114,92 +118,90 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Per-thread constants of the fused kernel: shared-memory offsets of the own
-// vector, of the vectors one row up/down (y neighbours) and of the edge
-// entries of the vectors to the left/right (x neighbours).  At the region
+// Per-thread constants of the fused kernel for a thread owning R consecutive
+// region rows: shared-memory offsets of its vector in each row, of the
+// vectors above its first row and below its last row (its other y
+// neighbours are its own rows, in registers), and of the edge entries of
+// the vectors left/right of it in each row (x neighbours).  At the region
 // border the offsets are clamped in bounds; the values read there only feed
 // halo points that never reach an output.
+template <int R>
 struct FusedLane {
-    int own, ym, yp, eo, el, er;
+    int own[R], ym, yp, eo[R], el[R], er[R];
 };
 
-// delta[i] = dt * A(nu_s) y at the V points of this thread's vector: c, zm,
-// zp are the vector at planes p, p-1, p+1 (registers); the y neighbours come
-// from the shared plane Sp, the x neighbours from its edge arrays
-// (E[1] = last element of each vector, E[0] = first element).
-template <typename T>
-__device__ __forceinline__ void stage_delta(T (&d)[VecT<T>::V], const T *__restrict__ Sp,
-                                            const T *__restrict__ E, int EL, const FusedLane &L,
-                                            const T (&c)[VecT<T>::V], const T (&zm)[VecT<T>::V],
-                                            const T (&zp)[VecT<T>::V], const T (&w)[7])
+// d[r][i] = dt * A(nu_s) y at the V points of row r of this thread: c, zm,
+// zp are the rows' vectors at planes p, p-1, p+1 (registers); the y
+// neighbours outside the thread's rows come from the shared plane Sp, the x
+// neighbours from its edge arrays (E[1] = last element of each vector, E[0]
+// = first element).  The seven terms are summed in a fixed order (centre,
+// x-1, x+1, y-1, y+1, z-1, z+1) whatever the thread's row count.
+template <typename T, int R>
+__device__ __forceinline__ void stage_delta(T (&d)[R][VecT<T>::V], const T *__restrict__ Sp,
+                                            const T *__restrict__ E, int EL, const FusedLane<R> &L,
+                                            const T (&c)[R][VecT<T>::V], const T (&zm)[R][VecT<T>::V],
+                                            const T (&zp)[R][VecT<T>::V], const T (&w)[7])
 {
     constexpr int V = VecT<T>::V;
     T ym[V], yp[V];
     ldv<T>(Sp + L.ym, ym);
     ldv<T>(Sp + L.yp, yp);
-    const T left = E[EL + L.el];
-    const T right = E[L.er];
 #pragma unroll
-    for (int i = 0; i < V; ++i) {
-        const T l = (i == 0) ? left : c[i - 1];
-        const T r = (i == V - 1) ? right : c[i + 1];
-        T acc = w[0] * c[i];
-        acc = fma(w[1], l, acc);
-        acc = fma(w[2], r, acc);
-        acc = fma(w[3], ym[i], acc);
-        acc = fma(w[4], yp[i], acc);
-        acc = fma(w[5], zm[i], acc);
-        acc = fma(w[6], zp[i], acc);
-        d[i] = acc;
+    for (int r = 0; r < R; ++r) {
+        const T left = E[EL + L.el[r]];
+        const T right = E[L.er[r]];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const T l = (i == 0) ? left : c[r][i > 0 ? i - 1 : 0];
+            const T rt = (i == V - 1) ? right : c[r][i < V - 1 ? i + 1 : 0];
+            const T up = (r == 0) ? ym[i] : c[r > 0 ? r - 1 : 0][i];
+            const T dn = (r == R - 1) ? yp[i] : c[r < R - 1 ? r + 1 : 0][i];
+            T acc = w[0] * c[r][i];
+            acc = fma(w[1], l, acc);
+            acc = fma(w[2], rt, acc);
+            acc = fma(w[3], up, acc);
+            acc = fma(w[4], dn, acc);
+            acc = fma(w[5], zm[r][i], acc);
+            acc = fma(w[6], zp[r][i], acc);
+            d[r][i] = acc;
+        }
     }
 }
 
-// y[i] = base[i] + (w . stencil)[i]: the weighted 7-point sum of stage_delta
-// accumulated onto base in one FMA chain (the stage's RK4 factor is folded
-// into w).
-template <typename T>
-__device__ __forceinline__ void stage_axpy(T (&y)[VecT<T>::V], const T *__restrict__ Sp,
-                                           const T *__restrict__ E, int EL, const FusedLane &L,
-                                           const T (&c)[VecT<T>::V], const T (&zm)[VecT<T>::V],
-                                           const T (&zp)[VecT<T>::V], const T (&w)[7],
-                                           const T (&base)[VecT<T>::V])
+// y[r][i] = base[r][i] + (w . stencil)[r][i]: the weighted 7-point sum of
+// stage_delta accumulated onto base in one FMA chain (the stage's RK4 factor
+// is folded into w).
+template <typename T, int R>
+__device__ __forceinline__ void stage_axpy(T (&y)[R][VecT<T>::V], const T *__restrict__ Sp,
+                                           const T *__restrict__ E, int EL, const FusedLane<R> &L,
+                                           const T (&c)[R][VecT<T>::V], const T (&zm)[R][VecT<T>::V],
+                                           const T (&zp)[R][VecT<T>::V], const T (&w)[7],
+                                           const T (&base)[R][VecT<T>::V])
 {
     constexpr int V = VecT<T>::V;
     T ym[V], yp[V];
     ldv<T>(Sp + L.ym, ym);
     ldv<T>(Sp + L.yp, yp);
-    const T left = E[EL + L.el];
-    const T right = E[L.er];
 #pragma unroll
-    for (int i = 0; i < V; ++i) {
-        const T l = (i == 0) ? left : c[i - 1];
-        const T r = (i == V - 1) ? right : c[i + 1];
-        T acc = fma(w[0], c[i], base[i]);
-        acc = fma(w[1], l, acc);
-        acc = fma(w[2], r, acc);
-        acc = fma(w[3], ym[i], acc);
-        acc = fma(w[4], yp[i], acc);
-        acc = fma(w[5], zm[i], acc);
-        acc = fma(w[6], zp[i], acc);
-        y[i] = acc;
+    for (int r = 0; r < R; ++r) {
+        const T left = E[EL + L.el[r]];
+        const T right = E[L.er[r]];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const T l = (i == 0) ? left : c[r][i > 0 ? i - 1 : 0];
+            const T rt = (i == V - 1) ? right : c[r][i < V - 1 ? i + 1 : 0];
+            const T up = (r == 0) ? ym[i] : c[r > 0 ? r - 1 : 0][i];
+            const T dn = (r == R - 1) ? yp[i] : c[r < R - 1 ? r + 1 : 0][i];
+            T acc = fma(w[0], c[r][i], base[r][i]);
+            acc = fma(w[1], l, acc);
+            acc = fma(w[2], rt, acc);
+            acc = fma(w[3], up, acc);
+            acc = fma(w[4], dn, acc);
+            acc = fma(w[5], zm[r][i], acc);
+            acc = fma(w[6], zp[r][i], acc);
+            y[r][i] = acc;
+        }
     }
-}
-
-// Elementwise helpers over a thread's vector: z = fma(a, x, y), z = x + y.
-template <typename T>
-__device__ __forceinline__ void vfma(T (&z)[VecT<T>::V], T a, const T (&x)[VecT<T>::V],
-                                     const T (&y)[VecT<T>::V])
-{
-#pragma unroll
-    for (int i = 0; i < VecT<T>::V; ++i) z[i] = fma(a, x[i], y[i]);
-}
-// z[i] = x[i] + y[i]
-template <typename T>
-__device__ __forceinline__ void vadd(T (&z)[VecT<T>::V], const T (&x)[VecT<T>::V],
-                                     const T (&y)[VecT<T>::V])
-{
-#pragma unroll
-    for (int i = 0; i < VecT<T>::V; ++i) z[i] = x[i] + y[i];
 }
 
 // Register windows of one thread, indexed by iteration modulo their period:
@@ -210,18 +212,18 @@ __device__ __forceinline__ void vadd(T (&z)[VecT<T>::V], const T (&x)[VecT<T>::V
 // which equals u + d1/6 + d2/3 + d3/3 + d4/6 (y2 = u + d1/2, y3 = u + d2/2,
 // y4 = u + d3) and needs no running increment sum; the differences y - u
 // are exact where y is within a factor 2 of u.
-template <typename T>
+template <typename T, int R>
 struct FusedRegs {
-    T U[4][VecT<T>::V];
-    T Y2[4][VecT<T>::V], Y3[3][VecT<T>::V], Y4[3][VecT<T>::V];
+    T U[4][R][VecT<T>::V];
+    T Y2[4][R][VecT<T>::V], Y3[3][R][VecT<T>::V], Y4[3][R][VecT<T>::V];
 };
 
 // Everything one z-iteration needs besides the registers.
-template <typename T>
+template <typename T, int R>
 struct FusedIter {
     T *ring, *planes, *ering, *eplanes;   // shared memory
-    const T *src;                          // global: this thread's column, plane 0
-    T *dst;
+    const T *src[R];                       // global: this thread's column in each row, plane 0
+    T *dst[R];
     long long plane;                       // n*n
     int n, n_it, zreq;                     // iterations, wrapped plane of the next request
     long long ooff;                        // output offset of the current iteration
@@ -229,27 +231,33 @@ struct FusedIter {
 };
 
 // One z-iteration at compile-time phase PH = it % 12 (see the kernel).
-template <typename T, int TX, int TY, int PH>
-__device__ __forceinline__ void fused_step(FusedIter<T> &I, FusedRegs<T> &R, const FusedLane &L,
-                                           int it, const T (&w1)[7], const T (&w2)[7],
-                                           const T (&w4)[7])
+template <typename T, int TX, int TY, int R, int PH>
+__device__ __forceinline__ void fused_step(FusedIter<T, R> &I, FusedRegs<T, R> &G,
+                                           const FusedLane<R> &L, int it, const T (&w1)[7],
+                                           const T (&w2)[7], const T (&w4)[7])
 {
-    using S = FusedShape<T, TX, TY>;
+    using S = FusedShape<T, TX, TY, R>;
     constexpr int V = S::V, PL = S::PL, EL = S::EL, D = S::D, RING = S::RING;
     constexpr T c3 = (T)(1.0 / 3.0);
     if (it >= I.n_it) return;
     // request the u plane of iteration it + D
-    if (it + D < I.n_it)
-        cp_async16(I.ring + ((PH + D) % RING) * PL + L.own, I.src + (long long)I.zreq * I.plane);
+    if (it + D < I.n_it) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            cp_async16(I.ring + ((PH + D) % RING) * PL + L.own[r], I.src[r] + (long long)I.zreq * I.plane);
+    }
     cp_async_commit();
     I.zreq = I.zreq + 1 == I.n ? 0 : I.zreq + 1;
     cp_async_wait<D>();
-    T un[V];
-    ldv<T>(I.ring + (PH % RING) * PL + L.own, un);
-    // edges of u(it) for the x neighbours of stage 1 in the next iteration
+    T un[R][V];
     T *eu = I.ering + (PH % RING) * 2 * EL;
-    eu[L.eo] = un[0];
-    eu[EL + L.eo] = un[V - 1];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        ldv<T>(I.ring + (PH % RING) * PL + L.own[r], un[r]);
+        // edges of u(it) for the x neighbours of stage 1 in the next iteration
+        eu[L.eo[r]] = un[r][0];
+        eu[EL + L.eo[r]] = un[r][V - 1];
+    }
 
     const T *Su = I.ring + ((PH + RING - 1) % RING) * PL;
     const T *Eu = I.ering + ((PH + RING - 1) % RING) * 2 * EL;
@@ -260,71 +268,92 @@ __device__ __forceinline__ void fused_step(FusedIter<T> &I, FusedRegs<T> &R, con
 
     // w1, w2 carry the factor 1/2 of y2 = u + d1/2 and y3 = u + d2/2, w4 the
     // factor 1/6 of d4 in the result, so each stage is one FMA chain
-    T y2n[V] = {}, y3n[V] = {}, y4n[V] = {};
+    T y2n[R][V] = {}, y3n[R][V] = {}, y4n[R][V] = {};
     // stage 1 at the plane of iteration it-1
     if (I.act1)
-        stage_axpy<T>(y2n, Su, Eu, EL, L, R.U[(PH + 3) % 4], R.U[(PH + 2) % 4], un, w1,
-                      R.U[(PH + 3) % 4]);
+        stage_axpy<T, R>(y2n, Su, Eu, EL, L, G.U[(PH + 3) % 4], G.U[(PH + 2) % 4], un, w1,
+                         G.U[(PH + 3) % 4]);
     // stage 2 at the plane of iteration it-2
     if (I.act2)
-        stage_axpy<T>(y3n, Sc, Ec, EL, L, R.Y2[(PH + 3) % 4], R.Y2[(PH + 2) % 4], y2n, w2,
-                      R.U[(PH + 2) % 4]);
+        stage_axpy<T, R>(y3n, Sc, Ec, EL, L, G.Y2[(PH + 3) % 4], G.Y2[(PH + 2) % 4], y2n, w2,
+                         G.U[(PH + 2) % 4]);
     // stage 3 at the plane of iteration it-3: y4 = u + d3 = u + 2 (d3 / 2)
     if (I.act3) {
-        T h[V];
-        stage_delta<T>(h, Sc + PL, Ec + 2 * EL, EL, L, R.Y3[(PH + 2) % 3], R.Y3[(PH + 1) % 3], y3n, w2);
-        vfma<T>(y4n, (T)2, h, R.U[(PH + 1) % 4]);
+        T h[R][V];
+        stage_delta<T, R>(h, Sc + PL, Ec + 2 * EL, EL, L, G.Y3[(PH + 2) % 3], G.Y3[(PH + 1) % 3],
+                          y3n, w2);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int i = 0; i < V; ++i) y4n[r][i] = fma((T)2, h[r][i], G.U[(PH + 1) % 4][r][i]);
     }
     // stage 4 at the plane of iteration it-4: the finished step
     //   u' = u + ((y2 - u) + 2 (y3 - u) + (y4 - u)) / 3 + d4 / 6
     if (I.act4 && it >= 8) {
-        const T(&u4)[V] = R.U[PH % 4];
-        const T(&y2c)[V] = R.Y2[(PH + 1) % 4];
-        const T(&y3c)[V] = R.Y3[(PH + 1) % 3];
-        const T(&y4c)[V] = R.Y4[(PH + 2) % 3];
-        T b[V], o[V];
+        const T(&u4)[R][V] = G.U[PH % 4];
+        const T(&y2c)[R][V] = G.Y2[(PH + 1) % 4];
+        const T(&y3c)[R][V] = G.Y3[(PH + 1) % 3];
+        const T(&y4c)[R][V] = G.Y4[(PH + 2) % 3];
+        T b[R][V], o[R][V];
 #pragma unroll
-        for (int i = 0; i < V; ++i) {
-            const T s = fma((T)2, y3c[i] - u4[i], (y2c[i] - u4[i]) + (y4c[i] - u4[i]));
-            b[i] = fma(c3, s, u4[i]);
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const T s = fma((T)2, y3c[r][i] - u4[r][i], (y2c[r][i] - u4[r][i]) + (y4c[r][i] - u4[r][i]));
+                b[r][i] = fma(c3, s, u4[r][i]);
+            }
+        stage_axpy<T, R>(o, Sc + 2 * PL, Ec + 4 * EL, EL, L, y4c, G.Y4[(PH + 1) % 3], y4n, w4, b);
+        if (I.owner) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) stv<T>(I.dst[r] + I.ooff, o[r]);
         }
-        stage_axpy<T>(o, Sc + 2 * PL, Ec + 4 * EL, EL, L, y4c, R.Y4[(PH + 1) % 3], y4n, w4, b);
-        if (I.owner) stv<T>(I.dst + I.ooff, o);
     }
     I.ooff += I.plane;
-    stv<T>(Sn + L.own, y2n);
-    stv<T>(Sn + PL + L.own, y3n);
-    stv<T>(Sn + 2 * PL + L.own, y4n);
-    En[L.eo] = y2n[0];
-    En[EL + L.eo] = y2n[V - 1];
-    En[2 * EL + L.eo] = y3n[0];
-    En[3 * EL + L.eo] = y3n[V - 1];
-    En[4 * EL + L.eo] = y4n[0];
-    En[5 * EL + L.eo] = y4n[V - 1];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        stv<T>(Sn + L.own[r], y2n[r]);
+        stv<T>(Sn + PL + L.own[r], y3n[r]);
+        stv<T>(Sn + 2 * PL + L.own[r], y4n[r]);
+        En[L.eo[r]] = y2n[r][0];
+        En[EL + L.eo[r]] = y2n[r][V - 1];
+        En[2 * EL + L.eo[r]] = y3n[r][0];
+        En[3 * EL + L.eo[r]] = y3n[r][V - 1];
+        En[4 * EL + L.eo[r]] = y4n[r][0];
+        En[5 * EL + L.eo[r]] = y4n[r][V - 1];
+    }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < V; ++i) {
-        R.U[PH % 4][i] = un[i];
-        R.Y2[PH % 4][i] = y2n[i];
-        R.Y3[PH % 3][i] = y3n[i];
-        R.Y4[PH % 3][i] = y4n[i];
-    }
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            G.U[PH % 4][r][i] = un[r][i];
+            G.Y2[PH % 4][r][i] = y2n[r][i];
+            G.Y3[PH % 3][r][i] = y3n[r][i];
+            G.Y4[PH % 3][r][i] = y4n[r][i];
+        }
 }
 
 // One RK4 step of `count` fields.  Each CTA owns a TX x TY column (plus a
-// 4-point halo in x and y) of one field and a z range [z_lo, z_hi); it runs
-// n_it = (z_hi - z_lo) + 8 iterations, iteration it loading plane
+// 4-point halo in x and y) of one field and a z range [z_lo, z_hi); each
+// thread owns one V-vector in each of R consecutive region rows.  The CTA
+// runs n_it = (z_hi - z_lo) + 8 iterations, iteration it loading plane
 // z_lo - 4 + it and finishing plane z_lo - 8 + it (stage s works on plane
 // z_lo - 4 + it - s).  The z loop is unrolled by 12, a multiple of every
 // register window's period, so the windows never move between registers.
-template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(FusedShape<T, TX, TY>::NT, FusedShape<T, TX, TY>::MINB)
+// With R = 2 a thread's own rows are each other's y neighbours, so per
+// stage it reads one shared-memory row above and one below for two rows of
+// results: a quarter less shared-memory traffic per point than R = 1.
+template <typename T, int TX, int TY, int R>
+__global__ void __launch_bounds__(FusedShape<T, TX, TY, R>::NT, FusedShape<T, TX, TY, R>::MINB)
 rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int tiles_x,
                  int tiles_y, int zchunk, int nzc)
 {
-    using S = FusedShape<T, TX, TY>;
+    using S = FusedShape<T, TX, TY, R>;
     constexpr int V = S::V, RX = S::RX, RY = S::RY, QX = S::QX, PL = S::PL, EL = S::EL;
     constexpr int D = S::D, RING = S::RING;
+    constexpr int H = 4 / R;                       // halo row groups per side
+    constexpr int RG = RY / R;                     // row groups in the region
+    static_assert(TY % R == 0 && 4 % R == 0, "row groups must tile the region");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *ring = reinterpret_cast<T *>(smem_raw);
     T *planes = ring + RING * PL;
@@ -333,14 +362,15 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
     __shared__ T s_w[3][7];                        // stage 1, stages 2-3, stage 4
 
     const int tid = threadIdx.x;
-    // Rows in order of the stages they need: the TY inner rows (all four)
-    // first, then the halo rows 3, RY-4 (three stages), 2, RY-3, 1, RY-2 and
-    // 0, RY-1 (none), so the halo rows share warps and those warps skip
-    // whole stages.
+    // Row groups (R rows each) in order of the stages they need: the TY/R
+    // inner groups (all four) first, then the halo groups from the innermost
+    // outwards, alternating top and bottom, so the halo groups share warps
+    // and those warps skip whole stages.
     const int qx = tid % QX;
-    const int ri = tid / QX;
-    const int hj = ri - TY;
-    const int ry = ri < TY ? 4 + ri : ((hj & 1) ? RY - 4 + (hj >> 1) : 3 - (hj >> 1));
+    const int gi = tid / QX;
+    const int hj = gi - TY / R;
+    const int grp = gi < TY / R ? H + gi : ((hj & 1) ? RG - H + (hj >> 1) : H - 1 - (hj >> 1));
+    const int ry = grp * R;                        // first region row of this thread
     int b = blockIdx.x;
     const int zc = b % nzc; b /= nzc;
     const int tx = b % tiles_x; b /= tiles_x;
@@ -369,24 +399,36 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
         w4[k] = s_w[2][k];
     }
 
-    FusedLane L;
-    L.own = ry * RX + qx * V;
-    L.ym = (ry > 0 ? ry - 1 : 0) * RX + qx * V;
-    L.yp = (ry < RY - 1 ? ry + 1 : RY - 1) * RX + qx * V;
-    L.eo = ry * QX + qx;
-    L.el = ry * QX + (qx > 0 ? qx - 1 : 0);          // right edge of the left vector
-    L.er = ry * QX + (qx < QX - 1 ? qx + 1 : QX - 1); // left edge of the right vector
+    // Shared-memory row of region row y: rows are stored grouped by their
+    // position within a row group (y % R), so when a warp's lanes span
+    // consecutive row groups, each of its accesses covers consecutive stored
+    // rows, as with one row per thread (no bank conflicts between groups).
+    auto prow = [](int y) { return (y % R) * RG + y / R; };
+    FusedLane<R> L;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int pr = prow(ry + r);
+        L.own[r] = pr * RX + qx * V;
+        L.eo[r] = pr * QX + qx;
+        L.el[r] = pr * QX + (qx > 0 ? qx - 1 : 0);          // right edge of the left vector
+        L.er[r] = pr * QX + (qx < QX - 1 ? qx + 1 : QX - 1); // left edge of the right vector
+    }
+    L.ym = prow(ry > 0 ? ry - 1 : 0) * RX + qx * V;
+    L.yp = prow(ry + R < RY ? ry + R : RY - 1) * RX + qx * V;
 
     const int gx = ((tx * TX - 4 + qx * V) % n + n) % n;
-    const int gy = ((ty * TY - 4 + ry) % n + n) % n;
-    FusedIter<T> I;
+    FusedIter<T, R> I;
     I.ring = ring;
     I.planes = planes;
     I.ering = ering;
     I.eplanes = eplanes;
     I.plane = (long long)n * n;
-    I.src = in + (long long)f * a.P + (long long)gy * n + gx;
-    I.dst = out + (long long)f * a.P + (long long)gy * n + gx;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int gy = ((ty * TY - 4 + ry + r) % n + n) % n;
+        I.src[r] = in + (long long)f * a.P + (long long)gy * n + gx;
+        I.dst[r] = out + (long long)f * a.P + (long long)gy * n + gx;
+    }
     I.n = n;
     const int z_lo = zc * zchunk;
     const int z_hi = min(z_lo + zchunk, n);
@@ -394,7 +436,7 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
     I.ooff = (long long)(z_lo - 8) * I.plane;
     // stage s is needed on rows [s, RY-s) and elements [s, RX-s) of the region
     auto active = [&](int s) {
-        return ry >= s && ry < RY - s && (qx + 1) * V > s && qx * V < RX - s;
+        return ry + R - 1 >= s && ry < RY - s && (qx + 1) * V > s && qx * V < RX - s;
     };
     // warp-uniform stage flags: a warp takes a stage when any of its lanes
     // needs it (the other lanes' results there are never read), so the
@@ -404,6 +446,8 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
     I.act2 = __any_sync(lanes, active(2));
     I.act3 = __any_sync(lanes, active(3));
     I.act4 = __any_sync(lanes, active(4));
+    // the region's inner rows [4, 4+TY) are whole row groups (4 and TY are
+    // multiples of R), so a thread owns outputs in all of its rows or none
     I.owner = ry >= 4 && ry < 4 + TY && qx * V >= 4 && qx * V < 4 + TX;
 
     // prologue: planes of iterations 0 .. D-1 into ring slots 0 .. D-1
@@ -411,87 +455,98 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
     z0 = ((z0 % n) + n) % n;
 #pragma unroll
     for (int q = 0; q < D; ++q) {
-        if (q < I.n_it) cp_async16(ring + q * PL + L.own, I.src + (long long)z0 * I.plane);
+        if (q < I.n_it) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                cp_async16(ring + q * PL + L.own[r], I.src[r] + (long long)z0 * I.plane);
+        }
         cp_async_commit();
         z0 = z0 + 1 == n ? 0 : z0 + 1;
     }
     I.zreq = z0;
 
-    FusedRegs<T> R;
+    FusedRegs<T, R> G;
 #pragma unroll
-    for (int i = 0; i < V; ++i) {
+    for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) R.U[k][i] = R.Y2[k][i] = (T)0;
+        for (int i = 0; i < V; ++i) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) R.Y3[k][i] = R.Y4[k][i] = (T)0;
-    }
+            for (int k = 0; k < 4; ++k) G.U[k][r][i] = G.Y2[k][r][i] = (T)0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) G.Y3[k][r][i] = G.Y4[k][r][i] = (T)0;
+        }
     for (int base = 0; base < I.n_it; base += 12) {
-        fused_step<T, TX, TY, 0>(I, R, L, base + 0, w1, w2, w4);
-        fused_step<T, TX, TY, 1>(I, R, L, base + 1, w1, w2, w4);
-        fused_step<T, TX, TY, 2>(I, R, L, base + 2, w1, w2, w4);
-        fused_step<T, TX, TY, 3>(I, R, L, base + 3, w1, w2, w4);
-        fused_step<T, TX, TY, 4>(I, R, L, base + 4, w1, w2, w4);
-        fused_step<T, TX, TY, 5>(I, R, L, base + 5, w1, w2, w4);
-        fused_step<T, TX, TY, 6>(I, R, L, base + 6, w1, w2, w4);
-        fused_step<T, TX, TY, 7>(I, R, L, base + 7, w1, w2, w4);
-        fused_step<T, TX, TY, 8>(I, R, L, base + 8, w1, w2, w4);
-        fused_step<T, TX, TY, 9>(I, R, L, base + 9, w1, w2, w4);
-        fused_step<T, TX, TY, 10>(I, R, L, base + 10, w1, w2, w4);
-        fused_step<T, TX, TY, 11>(I, R, L, base + 11, w1, w2, w4);
+        fused_step<T, TX, TY, R, 0>(I, G, L, base + 0, w1, w2, w4);
+        fused_step<T, TX, TY, R, 1>(I, G, L, base + 1, w1, w2, w4);
+        fused_step<T, TX, TY, R, 2>(I, G, L, base + 2, w1, w2, w4);
+        fused_step<T, TX, TY, R, 3>(I, G, L, base + 3, w1, w2, w4);
+        fused_step<T, TX, TY, R, 4>(I, G, L, base + 4, w1, w2, w4);
+        fused_step<T, TX, TY, R, 5>(I, G, L, base + 5, w1, w2, w4);
+        fused_step<T, TX, TY, R, 6>(I, G, L, base + 6, w1, w2, w4);
+        fused_step<T, TX, TY, R, 7>(I, G, L, base + 7, w1, w2, w4);
+        fused_step<T, TX, TY, R, 8>(I, G, L, base + 8, w1, w2, w4);
+        fused_step<T, TX, TY, R, 9>(I, G, L, base + 9, w1, w2, w4);
+        fused_step<T, TX, TY, R, 10>(I, G, L, base + 10, w1, w2, w4);
+        fused_step<T, TX, TY, R, 11>(I, G, L, base + 11, w1, w2, w4);
     }
     cp_async_wait<0>();
 }
 
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, int R>
 static cudaError_t launch_fused_shape(const StepArgs &a, const T *in, T *out, int zchunk,
                                       cudaStream_t st)
 {
-    using S = FusedShape<T, TX, TY>;
+    using S = FusedShape<T, TX, TY, R>;
     const int tiles_x = a.n / TX, tiles_y = a.n / TY;
     const int nzc = (a.n + zchunk - 1) / zchunk;
     const long long blocks = (long long)a.count * tiles_x * tiles_y * nzc;
-    rk4_fused_kernel<T, TX, TY><<<(unsigned)blocks, S::NT, S::SMEM, st>>>(a, in, out, tiles_x,
-                                                                         tiles_y, zchunk, nzc);
+    rk4_fused_kernel<T, TX, TY, R><<<(unsigned)blocks, S::NT, S::SMEM, st>>>(a, in, out, tiles_x,
+                                                                            tiles_y, zchunk, nzc);
     return cudaGetLastError();
 }
 
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, int R>
 static cudaError_t configure_shape()
 {
-    return cudaFuncSetAttribute(rk4_fused_kernel<T, TX, TY>,
+    return cudaFuncSetAttribute(rk4_fused_kernel<T, TX, TY, R>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)FusedShape<T, TX, TY>::SMEM);
+                                (int)FusedShape<T, TX, TY, R>::SMEM);
 }
 
-// Tile shapes compiled for the fused kernel.
+// Tile shapes compiled for the fused kernel: element type, tile, rows per thread.
 #define PR_FUSED_SHAPES(X) \
-    X(float, 64, 32)       \
-    X(float, 64, 16)       \
-    X(float, 64, 8)        \
-    X(float, 32, 16)       \
-    X(float, 32, 8)        \
-    X(float, 16, 16)       \
-    X(double, 32, 8)       \
-    X(double, 16, 16)      \
-    X(double, 16, 8)
+    X(float, 64, 32, 1)    \
+    X(float, 64, 16, 1)    \
+    X(float, 64, 8, 1)     \
+    X(float, 32, 16, 1)    \
+    X(float, 32, 8, 1)     \
+    X(float, 16, 16, 1)    \
+    X(float, 64, 32, 2)    \
+    X(float, 64, 16, 2)    \
+    X(float, 32, 32, 2)    \
+    X(float, 32, 16, 2)    \
+    X(double, 32, 8, 1)    \
+    X(double, 16, 16, 1)   \
+    X(double, 16, 8, 1)
 
 // Shared-memory opt-in of every compiled shape (once per device, before any
 // launch or stream capture).
 cudaError_t configure_rk4_kernels()
 {
     cudaError_t e = cudaSuccess;
-#define PR_CONF(T, TX, TY) \
-    if (e == cudaSuccess) e = configure_shape<T, TX, TY>();
+#define PR_CONF(T, TX, TY, R) \
+    if (e == cudaSuccess) e = configure_shape<T, TX, TY, R>();
     PR_FUSED_SHAPES(PR_CONF)
 #undef PR_CONF
     return e;
 }
 
-bool rk4_fused_supported(int dtype, int n, int tile_x, int tile_y)
+bool rk4_fused_supported(int dtype, int n, int tile_x, int tile_y, int rows)
 {
     if (n % tile_x || n % tile_y) return false;
-#define PR_SUP(T, TX, TY)                                                                   \
-    if ((dtype == PARAREAL_F64) == (sizeof(T) == 8) && tile_x == TX && tile_y == TY) return true;
+#define PR_SUP(T, TX, TY, R)                                                                 \
+    if ((dtype == PARAREAL_F64) == (sizeof(T) == 8) && tile_x == TX && tile_y == TY && rows == R) \
+        return true;
     PR_FUSED_SHAPES(PR_SUP)
 #undef PR_SUP
     return false;
@@ -499,20 +554,21 @@ bool rk4_fused_supported(int dtype, int n, int tile_x, int tile_y)
 
 template <typename T>
 cudaError_t launch_rk4_fused(const StepArgs &a, const T *in, T *out, int tile_x, int tile_y,
-                             int zchunk, cudaStream_t st)
+                             int zchunk, int rows, cudaStream_t st)
 {
     if (zchunk <= 0 || a.n % tile_x || a.n % tile_y) return cudaErrorInvalidValue;
-#define PR_DISPATCH(TT, TX, TY)                                                             \
+#define PR_DISPATCH(TT, TX, TY, R)                                                          \
     if constexpr (std::is_same<T, TT>::value)                                                \
-        if (tile_x == TX && tile_y == TY) return launch_fused_shape<TT, TX, TY>(a, in, out, zchunk, st);
+        if (tile_x == TX && tile_y == TY && rows == R)                                       \
+            return launch_fused_shape<TT, TX, TY, R>(a, in, out, zchunk, st);
     PR_FUSED_SHAPES(PR_DISPATCH)
 #undef PR_DISPATCH
     return cudaErrorInvalidValue;
 }
 template cudaError_t launch_rk4_fused<float>(const StepArgs &, const float *, float *, int, int,
-                                             int, cudaStream_t);
+                                             int, int, cudaStream_t);
 template cudaError_t launch_rk4_fused<double>(const StepArgs &, const double *, double *, int,
-                                              int, int, cudaStream_t);
+                                              int, int, int, cudaStream_t);
 
 // ------------------------------------------------------------ staged RK4
 
