@@ -445,7 +445,9 @@ def run_learned_128(args):
     fine solver generates) vs the stencil coarse propagator vs shift only vs
     serial fine: iterations and time to d^k <= 1e-6.  Two nets correct the
     stencil propagator: the GELU network as specified, and the linear one
-    (nu as a factor) with the correction applied to U^{k+1}[n] - U^k[n]."""
+    (nu as a factor) with the correction applied to U^{k+1}[n] - U^k[n]; the
+    linear one is timed layer by layer (BF16, tensor cores) and composed into
+    one 9^3 kernel per slice (FP32)."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -454,10 +456,10 @@ def run_learned_128(args):
     base, u0 = configs.fp32_128()
     n, N = base.n, base.n_slices
     mk = lambda kind, r, dtg, skip=native.SKIP_SHIFT, act=native.ACT_GELU, \
-        form=native.CORRECTION_STANDARD: native.Config.make(
+        form=native.CORRECTION_STANDARD, ev=native.EVAL_LAYERS: native.Config.make(
             n, N, base.T, base.dt_fine, dtg, r, fine_dtype=native.F32, coarse_kind=kind,
             nu0=base.nu0, nu_amp=base.nu_amp, nu_omega=base.nu_omega, learned_skip=skip,
-            learned_act=act, correction_form=form)
+            learned_act=act, correction_form=form, learned_eval=ev)
     # the nets correct the stencil propagator (RK4 on 32^3 at 1/256)
     learned = native.Parareal(mk(native.COARSE_LEARNED, base.coarse_factor, base.dt_coarse,
                                  native.SKIP_STENCIL))
@@ -487,9 +489,15 @@ def run_learned_128(args):
                        "train_s": time.perf_counter() - t0}
     del pu, pf
     torch.cuda.empty_cache()
+    # the trained linear net evaluated as one 9^3 kernel per slice
+    composed = native.Parareal(mk(native.COARSE_LEARNED, base.coarse_factor, base.dt_coarse,
+                                  native.SKIP_STENCIL, native.ACT_LINEAR,
+                                  native.CORRECTION_DIFFERENCE, native.EVAL_COMPOSED))
+    composed.set_coarse_model(linear.get_coarse_model())
     u = torch.from_numpy(u0).cuda()
     res = {}
-    ctxs = {"learned_linear": linear,
+    ctxs = {"learned_linear_composed": composed,
+            "learned_linear": linear,
             "learned_gelu": learned,
             "stencil": native.Parareal(base),
             "stencil_difference_form": native.Parareal(
@@ -521,6 +529,43 @@ def run_learned_128(args):
                                 "lr": args.lr, "pairs_s": pairs_s, **train}}))
     for c in ctxs.values():
         c.close()
+    return 0
+
+
+def run_learned_g(args):
+    """One application of the learned coarse propagator (128^3, N = 32,
+    stencil skip, linear network) per evaluation: layer by layer (BF16,
+    tensor cores) and composed into one 9^3 kernel (FP32), with perturbed
+    initial weights (the cost does not depend on their values); the stencil
+    propagator alone beside them.  A small, self-contained target for ncu."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1409_8563_gb300 import configs, inputs, native
+    base, u0 = configs.fp32_128()
+    mk = lambda kind, ev: native.Config.make(
+        128, 32, base.T, base.dt_fine, base.dt_coarse, base.coarse_factor, fine_dtype=native.F32,
+        coarse_kind=kind, nu0=base.nu0, nu_amp=base.nu_amp, nu_omega=base.nu_omega,
+        learned_skip=native.SKIP_STENCIL, learned_act=native.ACT_LINEAR,
+        correction_form=native.CORRECTION_DIFFERENCE, learned_eval=ev)
+    w = inputs.initial_weights(seed=0)
+    w = (w + 0.01 * np.random.default_rng(1).standard_normal(w.shape)).astype(np.float32)
+    src = torch.from_numpy(u0).cuda()
+    dst = torch.empty_like(src)
+    out = {"workload": "learned_g", "n": 128, "n_slices": 32}
+    for name, kind, ev in (("composed", native.COARSE_LEARNED, native.EVAL_COMPOSED),
+                           ("layers", native.COARSE_LEARNED, native.EVAL_LAYERS),
+                           ("stencil", native.COARSE_STENCIL, native.EVAL_LAYERS)):
+        c = native.Parareal(mk(kind, ev))
+        if kind == native.COARSE_LEARNED:
+            c.set_coarse_model(w)
+        for _ in range(args.warmup):
+            c.propagate(1, src, dst, 1, 1)
+        ms, _ = _timed(lambda: c.propagate(1, src, dst, 1, 1), max(args.steps, 1))
+        out[name + "_g_apply_ms"] = ms
+        c.close()
+    print(json.dumps(out))
     return 0
 
 
@@ -610,8 +655,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="fp32_256",
-                    choices=["fp32_256", "fp32_128", "fp64_32", "learned_128", "batch64",
-                             "fine_sweep", "paper_faithful"])
+                    choices=["fp32_256", "fp32_128", "fp64_32", "learned_128", "learned_g",
+                             "batch64", "fine_sweep", "paper_faithful"])
     ap.add_argument("--slices", type=int, default=8)
     ap.add_argument("--correction", default="difference", choices=["difference", "standard"],
                     help="evaluation of the Parareal correction (fp32_256 / fp32_128 / batch64)")
@@ -630,6 +675,8 @@ def main():
         return run_fp64_32(args)
     if args.workload == "learned_128":
         return run_learned_128(args)
+    if args.workload == "learned_g":
+        return run_learned_g(args)
     if args.workload == "batch64":
         return run_batch64(args)
     if args.workload == "fine_sweep":

@@ -118,6 +118,7 @@ typedef struct {
     int fine_scheme;       /* PARAREAL_SCHEME_*: spatial operator of F */
     int learned_act;       /* PARAREAL_ACT_*: the learned propagator's layers */
     int correction_form;   /* PARAREAL_CORRECTION_*: how Eq. (parareal) is evaluated */
+    int learned_eval;      /* PARAREAL_EVAL_*: how a LINEAR learned propagator is evaluated */
 } parareal_config;
 
 /* Layers of the learned coarse propagator (coarse_kind LEARNED / SHIFT):
@@ -127,6 +128,16 @@ typedef struct {
  *        nu(t_n)/nu0 * Sk(u) (Sk the skip propagator): G is then linear in u,
  *        with a kernel that depends on nu(t_n). */
 enum { PARAREAL_ACT_GELU = 0, PARAREAL_ACT_LINEAR = 1 };
+
+/* Evaluation of a LINEAR learned propagator (learned_act LINEAR):
+ * LAYERS   layer by layer: BF16 weights and activations, FP32 accumulation,
+ *          the 16 -> 16 layers on the tensor cores;
+ * COMPOSED the four linear layers composed into one 9x9x9 periodic
+ *          cross-correlation per slice, K_0 + nu(t_n)/nu0 K_1 (built in FP64
+ *          from the FP32 master weights whenever the model changes), applied
+ *          with FP32 accumulation: the same linear operator in about a
+ *          twentieth of the arithmetic.  No counterpart in the paper. */
+enum { PARAREAL_EVAL_LAYERS = 0, PARAREAL_EVAL_COMPOSED = 1 };
 
 /* Evaluation of the correction (Eq. parareal):
  * STANDARD   U^{k+1}[n+1] = F(U^k[n]) + (G(U^{k+1}[n]) - G(U^k[n])), as printed;

@@ -113,5 +113,46 @@ def adam_step(params, grads, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
             p -= lr * mhat / (np.sqrt(vhat) + eps)
 
 
+def compose_linear(params, nu_hat):
+    """The linear network (identity activations, biases unused) as one periodic
+    cross-correlation of its input x = S(u):
+
+        Net(x)[p] = sum_e K[e] x[p + e],   e in [-4, 4]^3,   K = K_0 + nu_hat K_1,
+
+    K_c the kernel of input channel c of layer 1 carried through layers 2-4.
+    Cross-correlations compose by adding offsets: (W2 (W1 x))[p] =
+    sum_{d1, d2} W2[d2] W1[d1] x[p + d1 + d2], channels contracted in between.
+    Returns K as [9][9][9], index (e_z + 4, e_y + 4, e_x + 4)."""
+    K = []
+    for ch in range(2):
+        A = np.asarray(params[0][0], dtype=np.float64)[:, ch]     # [16][3][3][3]
+        for W, _ in params[1:]:
+            W = np.asarray(W, dtype=np.float64)
+            r = A.shape[-1]
+            B = np.zeros((W.shape[0],) + (r + 2,) * 3)
+            for dz in range(3):
+                for dy in range(3):
+                    for dx in range(3):
+                        B[:, dz:dz + r, dy:dy + r, dx:dx + r] += np.einsum(
+                            "oi,izyx->ozyx", W[:, :, dz, dy, dx], A)
+            A = B
+        K.append(A[0])
+    return K[0] + float(nu_hat) * K[1]
+
+
+def apply_kernel(x, K):
+    """sum_e K[e] x[p + e] on a periodic [n][n][n] field, K of odd edge."""
+    x = np.asarray(x, dtype=np.float64)
+    R = K.shape[0] // 2
+    out = np.zeros_like(x)
+    for ez in range(-R, R + 1):
+        for ey in range(-R, R + 1):
+            for ex in range(-R, R + 1):
+                w = K[ez + R, ey + R, ex + R]
+                if w != 0.0:
+                    out += w * np.roll(x, (-ez, -ey, -ex), axis=(0, 1, 2))
+    return out
+
+
 def zeros_like_params(params):
     return [[np.zeros_like(W), np.zeros_like(b)] for W, b in params]

@@ -122,6 +122,11 @@ static parareal_status validate(const parareal_config *cfg, long long *Nf, long 
         return PARAREAL_E_INVALID;
     }
     if (cfg->learned_skip != PARAREAL_SKIP_SHIFT && cfg->learned_skip != PARAREAL_SKIP_STENCIL) { *msg = "learned_skip"; return PARAREAL_E_INVALID; }
+    if (cfg->learned_eval != PARAREAL_EVAL_LAYERS && cfg->learned_eval != PARAREAL_EVAL_COMPOSED) { *msg = "learned_eval"; return PARAREAL_E_INVALID; }
+    if (cfg->learned_eval == PARAREAL_EVAL_COMPOSED && cfg->learned_act != PARAREAL_ACT_LINEAR) {
+        *msg = "learned_eval COMPOSED needs learned_act LINEAR (a GELU network is not one convolution)";
+        return PARAREAL_E_INVALID;
+    }
     const double slice = cfg->T / cfg->n_slices;
     if (!is_integer_ratio(slice, cfg->dt_fine, Nf)) { *msg = "T/(n_slices dt_fine) must be an integer"; return PARAREAL_E_INVALID; }
     if (!is_integer_ratio(slice, cfg->dt_coarse, Nc)) { *msg = "T/(n_slices dt_coarse) must be an integer"; return PARAREAL_E_INVALID; }

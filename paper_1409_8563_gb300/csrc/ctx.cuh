@@ -38,6 +38,9 @@ struct NetState {
     double *h_loss = nullptr;
     int adam_t = 0;
     int lin = 0;               // linear mode (PARAREAL_ACT_LINEAR)
+    bool composed = false;     // linear mode evaluated as one 9^3 kernel per slice
+    double *kscratch = nullptr;             // composition scratch (device)
+    float *keff = nullptr;                  // per-slice 9^3 kernels (device)
     bool tc = false;           // 16 -> 16 layers on tcgen05 (grid edge a multiple of 16)
     int *tc_err = nullptr;     // device flag: a tensor-core completion wait ran out
     bool has_model = false;
@@ -128,6 +131,7 @@ parareal_status stencil_g_fine(parareal_ctx *c, const double *u, int s, double *
 
 // learned.cu
 parareal_status net_check(parareal_ctx *c);
+parareal_status net_compose(parareal_ctx *c);
 parareal_status net_setup(parareal_ctx *c);
 void net_free(parareal_ctx *c);
 template <typename TU, typename TG>

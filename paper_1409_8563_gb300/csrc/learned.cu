@@ -62,6 +62,12 @@ parareal_status net_setup(parareal_ctx *c)
               dalloc((void **)&S.B4f, 27 * 8 * 16 * 2) && dalloc((void **)&S.tc_err, sizeof(int)) &&
               dalloc((void **)&S.nu_slices, sizeof(float) * c->N) &&
               dalloc((void **)&S.ia, (size_t)S.Pm * 32) && dalloc((void **)&S.ib, (size_t)S.Pm * 32);
+    S.composed = S.lin && c->cfg.learned_eval == PARAREAL_EVAL_COMPOSED;
+    if (S.composed && S.m % 16)
+        return fail(c, PARAREAL_E_INVALID, "the composed learned propagator needs a grid edge that is a multiple of 16");
+    if (ok && S.composed)
+        ok = dalloc((void **)&S.kscratch, compose_scratch_doubles() * sizeof(double)) &&
+             dalloc((void **)&S.keff, sizeof(float) * NET_K9 * c->N);
     if (!ok) return fail(c, PARAREAL_E_NOMEM, "learned propagator allocation failed");
     std::vector<float> nus(c->N);
     for (int s = 0; s < c->N; ++s) nus[s] = (float)(nu_of(c->cfg, s * slice) / c->cfg.nu0);
@@ -73,6 +79,16 @@ parareal_status net_setup(parareal_ctx *c)
     CK(cudaMemsetAsync(S.mom2, 0, NET_PARAMS * 4, c->st));
     LK(launch_prepare_operands(S.master, S.W1q, S.B2f, S.B3f, S.B2b, S.B3b, S.W4q, S.B4f, c->st));
     S.has_model = c->cfg.coarse_kind == PARAREAL_COARSE_SHIFT;
+    return net_compose(c);
+}
+
+// Composed evaluation: rebuild the per-slice 9^3 kernels from the master
+// weights (stream-ordered; called whenever the model changes).
+parareal_status net_compose(parareal_ctx *c)
+{
+    NetState &S = c->net;
+    if (!S.composed) return PARAREAL_OK;
+    LK(launch_compose_linear(S.master, S.nu_slices, c->N, S.kscratch, S.keff, c->st));
     return PARAREAL_OK;
 }
 
@@ -81,7 +97,7 @@ void net_free(parareal_ctx *c)
     NetState &S = c->net;
     void *p[] = {S.master, S.grad, S.mom1, S.mom2, S.W1q, S.W4q, S.B2f, S.B3f, S.B2b, S.B3b, S.B4f, S.tc_err,
                  S.nu_slices, S.ia, S.ib, S.z1, S.z2, S.z3, S.a1, S.a2, S.a3, S.dzA, S.dzB, S.dz4,
-                 S.ub, S.fb, S.nub, S.partials, S.loss_parts, S.loss_sum};
+                 S.ub, S.fb, S.nub, S.partials, S.loss_parts, S.loss_sum, S.kscratch, S.keff};
     for (void *q : p)
         if (q) cudaFree(q);
     if (S.h_nub) cudaFreeHost(S.h_nub);
@@ -106,6 +122,11 @@ template <typename TU, typename TG>
 parareal_status net_apply(parareal_ctx *c, const TU *u, int slice, TG *out)
 {
     NetState &S = c->net;
+    if (S.composed) {
+        // the four linear layers as one 9^3 cross-correlation (net_composed.cu)
+        LK((launch_net_lin9<TU, TG>(u, S.m, S.shift, S.keff + (size_t)slice * NET_K9, out, c->st)));
+        return PARAREAL_OK;
+    }
     const float *b = S.master;
     LK(launch_net_in_fwd<TU>(u, S.m, S.shift, S.nu_slices + slice, 1, S.W1q, b + NET_B1, nullptr, S.ia, c->st,
                              S.lin));
@@ -237,6 +258,8 @@ extern "C" parareal_status parareal_set_coarse_model(parareal_ctx *c, const floa
     S.adam_t = 0;
     LK(launch_prepare_operands(S.master, S.W1q, S.B2f, S.B3f, S.B2b, S.B3b, S.W4q, S.B4f, c->st));
     if (mem == PARAREAL_MEM_HOST) CK(cudaStreamSynchronize(c->st));
+    s = net_compose(c);
+    if (s != PARAREAL_OK) return s;
     S.has_model = true;
     c->started = false;   // G changed: the next iterate restarts from the coarse chain
     c->k_total = 0;
@@ -337,6 +360,7 @@ extern "C" parareal_status parareal_train_coarse(parareal_ctx *c, const float *p
         if (!std::isfinite(tot)) return fail(c, PARAREAL_E_DIVERGED, "training loss is not finite");
         if (loss_hist) loss_hist[e] = tot / ((double)nbat * B * S.Pm);
     }
+    if ((s = net_compose(c)) != PARAREAL_OK) return s;
     S.has_model = true;
     c->started = false;
     c->k_total = 0;

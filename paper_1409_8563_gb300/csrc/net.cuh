@@ -16,6 +16,19 @@ constexpr int NET_MID_PARTIAL = 27 * 256 + 16;   // dW[27][16][16] + db[16]
 constexpr int NET_OUT_PARTIAL = 433;             // dW4[16][27] + db4
 constexpr int NET_IN_PARTIAL = 880;              // dW1[16][2][27] + db1[16]
 
+// LINEAR network composed into one 9x9x9 cross-correlation per slice
+// (net_composed.cu): taps [ez+4][ey+4][ex+4].
+constexpr int NET_K9 = 729;
+size_t compose_scratch_doubles();
+// keff[n] = K_0 + nu_hat[n] K_1 for n < n_slices (FP32), built in FP64 from
+// the master weights; scratch: compose_scratch_doubles() doubles.
+cudaError_t launch_compose_linear(const float *master, const float *nu_hat, int n_slices,
+                                  double *scratch, float *keff, cudaStream_t st);
+// out = S(u) + K * S(u) (S the periodic shift by s), K: NET_K9 floats on the
+// device, FP32 accumulation; m a multiple of 16.
+template <typename TU, typename TG>
+cudaError_t launch_net_lin9(const TU *u, int m, const int s[3], const float *K, TG *out, cudaStream_t st);
+
 cudaError_t configure_net_kernels();
 // 16 -> 16 forward layer on the 5th-generation tensor cores (net_tc.cu);
 // m a multiple of 16.  errflag (device int) is set if an MMA completion wait

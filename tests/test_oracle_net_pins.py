@@ -99,3 +99,37 @@ def test_linear_mode_is_linear_in_u_with_a_nu_dependent_kernel():
     assert np.allclose(G(2.0 * u - 0.5 * v), 2.0 * G(u) - 0.5 * G(v), atol=1e-12, rtol=0)
     assert not np.any(G(np.zeros_like(u)))
     assert np.max(np.abs(G(u, 0.9) - G(u, 1.3))) > 1e-3
+
+
+def test_composed_kernel_of_single_tap_layers_is_one_shifted_tap():
+    """Four layers that each copy channel 0 one cell along a fixed offset
+    compose into a single tap at the sum of the offsets, scaled by the product
+    of the weights (offsets add under composition of cross-correlations)."""
+    params = [[np.zeros((co, ci, 3, 3, 3)), np.zeros(co)] for ci, co in net.LAYERS]
+    offs = [(1, 0, 2), (2, 1, 1), (0, 2, 2), (2, 2, 0)]       # (kz, ky, kx) = offset + 1
+    scale = [0.5, -2.0, 3.0, 0.25]
+    for (W, _), o, a in zip(params, offs, scale):
+        W[0, 0][o] = a
+    params[0][0][0, 1][1, 1, 1] = 7.0      # channel 1: centre tap, then the same path
+    K = net.compose_linear(params, 0.3)
+    e = tuple(sum(o[i] - 1 for o in offs) + 4 for i in range(3))
+    want = np.zeros((9, 9, 9))
+    want[e] += 0.5 * -2.0 * 3.0 * 0.25
+    e1 = tuple(sum(o[i] - 1 for o in offs[1:]) + 4 for i in range(3))
+    want[e1] += 0.3 * 7.0 * -2.0 * 3.0 * 0.25
+    assert np.array_equal(K != 0, want != 0)
+    assert np.allclose(K, want, rtol=1e-15, atol=0)
+
+
+def test_linear_network_equals_its_composed_kernel():
+    """Net(S(u)) of the linear network, layer by layer, equals one 9^3
+    cross-correlation with the composed kernel (associativity of convolution)."""
+    n, s = 11, (2, 0, 1)
+    u = inputs.random_field(n, seed=5)
+    params = net.init_params(seed=3, scale=0.15)
+    for nu_hat in (0.6, 1.4):
+        g, _ = net.forward(u, nu_hat, params, s, linear=True)
+        su = core.shift(u, s)
+        K = net.compose_linear(params, nu_hat)
+        got = su + net.apply_kernel(su, K)
+        assert np.max(np.abs(got - g)) <= 1e-12 * np.max(np.abs(g)), np.max(np.abs(got - g))
