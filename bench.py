@@ -532,6 +532,81 @@ def run_learned_128(args):
     return 0
 
 
+def run_learned_512(args):
+    """512^3, N = 16 (dt_F = 1/32768, stencil G on 64^3 at 1/512): Parareal with
+    the linear learned propagator (stencil skip, composed evaluation,
+    difference-form correction), trained here on the pairs the fine solver
+    generates from --n-ics seeded fields (16 pairs each), against
+    stencil-G Parareal and the serial fine run: iterations and time to
+    d^k <= 1e-6, fine GLUP/s inside each solve.  One solve each (a solve
+    takes minutes at this size); contexts are built one after another to
+    bound the device memory (~160 GB at the peak, during training)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1409_8563_gb300 import configs, inputs, native
+    base, u0 = configs.fp32_512()
+    n, N = base.n, base.n_slices
+    P, nf = n ** 3, round(base.T / N / base.dt_fine)
+    mk = lambda kind, ev: native.Config.make(
+        n, N, base.T, base.dt_fine, base.dt_coarse, base.coarse_factor, fine_dtype=native.F32,
+        coarse_kind=kind, nu0=base.nu0, nu_amp=base.nu_amp, nu_omega=base.nu_omega,
+        learned_skip=native.SKIP_STENCIL, learned_act=native.ACT_LINEAR,
+        correction_form=native.CORRECTION_DIFFERENCE, learned_eval=ev)
+    out = {"workload": "learned_512", "n": n, "n_slices": N, "fine_steps_per_slice": nf}
+    # training (layer by layer, BF16, tensor cores)
+    t0 = time.perf_counter()
+    trainer = native.Parareal(mk(native.COARSE_LEARNED, native.EVAL_LAYERS))
+    n_ics = args.n_ics
+    ics = torch.stack([torch.from_numpy(inputs.spectral_ic(n, seed=1000 + i, kmax=32)
+                                        + 0.2 * inputs.random_field(n, seed=2000 + i)).float()
+                       for i in range(n_ics)]).cuda()
+    pu = torch.empty((n_ics * N, n, n, n), dtype=torch.float32, device="cuda")
+    pf = torch.empty_like(pu)
+    sl = trainer.make_pairs(ics, pu, pf)
+    torch.cuda.synchronize()
+    out["pairs"] = int(len(sl))
+    out["pairs_s"] = time.perf_counter() - t0
+    del ics
+    trainer.set_coarse_model(inputs.initial_weights(seed=0))
+    t0 = time.perf_counter()
+    hist = trainer.train_coarse(pu, pf, sl, epochs=args.epochs, batch=1, lr=args.lr, seed=1)
+    torch.cuda.synchronize()
+    out["train"] = {"epochs": args.epochs, "batch": 1, "lr": args.lr,
+                    "loss_first_last": [float(hist[0]), float(hist[-1])],
+                    "train_s": time.perf_counter() - t0}
+    w = trainer.get_coarse_model()
+    trainer.close()
+    del pu, pf
+    torch.cuda.empty_cache()
+    u = torch.from_numpy(u0).cuda()
+    ref = torch.empty((n,) * 3, dtype=torch.float64, device="cuda")
+    runs = {}
+    for name, kind in (("stencil_difference_form", native.COARSE_STENCIL),
+                       ("learned_linear_composed", native.COARSE_LEARNED)):
+        c = native.Parareal(mk(kind, native.EVAL_COMPOSED if kind == native.COARSE_LEARNED
+                               else native.EVAL_LAYERS))
+        c.autotune(TUNE_CACHE)
+        if kind == native.COARSE_LEARNED:
+            c.set_coarse_model(w)
+        c.set_problem(u)
+        if "serial_fine_ms" not in out:
+            ms, _ = _timed(lambda: c.serial_fine(ref, as_reference=True))
+            out["serial_fine_ms"] = ms
+            out["serial_fine_glups"] = P * N * nf / ms / 1e6
+        else:
+            c.set_reference(ref)
+        ms, (k, h) = _timed(lambda: c.iterate(N, TOL, native.STOP_DEFECT))
+        ups = sum(N - j for j in range(k)) * P * nf
+        runs[name] = {"k_star": k, "time_to_1e-6_ms": ms, "glups_in_solve": ups / ms / 1e6,
+                      "defects": [float(x) for x in h[:, 2]],
+                      "launch_shape_fine": list(c.launch_shape()[0])}
+        c.close()
+    out["runs"] = runs
+    print(json.dumps(out))
+    return 0
+
+
 def run_learned_g(args):
     """One application of the learned coarse propagator (128^3, N = 32,
     stencil skip, linear network) per evaluation: layer by layer (BF16,
@@ -655,8 +730,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="fp32_256",
-                    choices=["fp32_256", "fp32_128", "fp64_32", "learned_128", "learned_g",
-                             "batch64", "fine_sweep", "paper_faithful"])
+                    choices=["fp32_256", "fp32_128", "fp64_32", "learned_128", "learned_512",
+                             "learned_g", "batch64", "fine_sweep", "paper_faithful"])
     ap.add_argument("--slices", type=int, default=8)
     ap.add_argument("--correction", default="difference", choices=["difference", "standard"],
                     help="evaluation of the Parareal correction (fp32_256 / fp32_128 / batch64)")
@@ -677,6 +752,8 @@ def main():
         return run_learned_128(args)
     if args.workload == "learned_g":
         return run_learned_g(args)
+    if args.workload == "learned_512":
+        return run_learned_512(args)
     if args.workload == "batch64":
         return run_batch64(args)
     if args.workload == "fine_sweep":
