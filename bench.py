@@ -101,6 +101,17 @@ class ClockSampler:
                 out, _ = self.proc.communicate()
             self.lines = [l for l in out.splitlines() if l.strip()]
 
+    def power_w(self):
+        """Mean board power (W) over the samples, or None."""
+        pw = []
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                pw.append(float(f[2]))
+            except (ValueError, IndexError):
+                continue
+        return statistics.mean(pw) if pw else None
+
     def summary(self):
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -281,6 +292,17 @@ def run(args):
     fine_ms, fine_launches, fine_bytes = ctx.profile_read()
     ctx.profile(False)
     launches = ctx.launch_count() - launches0
+    # energy of the serial fine run for comparison: board power sampled over
+    # enough repetitions to span a few seconds
+    reps = max(1, int(round(3000.0 / max(serial_ms, 1.0))))
+    with ClockSampler(local) as clk_s:
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(reps):
+                ctx.serial_fine(None, as_reference=True)
+            ev1.record(stream)
+        ev1.synchronize()
+    serial_rep_ms = ev0.elapsed_time(ev1) / reps
     total_ms = max_over_ranks(dist, sum(step_ms))
     updates = sum_over_ranks(dist, updates)
     value = updates / (total_ms / 1000.0) / 1e9
@@ -316,6 +338,16 @@ def run(args):
                          f"{dt:.1f} s)"}
 
     clocks = clk.summary()
+    p_par, p_ser = clk.power_w(), clk_s.power_w()
+    energy = None
+    if p_par is not None and p_ser is not None:
+        e_par = p_par * total_ms / args.steps / 1000.0
+        e_ser = p_ser * serial_rep_ms / 1000.0
+        energy = {"parareal_j": e_par, "serial_fine_j": e_ser, "ratio": e_par / e_ser,
+                  "power_w_parareal": p_par, "power_w_serial_fine": p_ser,
+                  "what": "GPU board power (nvidia-smi, every 200 ms) x CUDA-event time per "
+                          "solve; the paper's node, network and cooling terms are not "
+                          "measurable here"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -342,6 +374,7 @@ def run(args):
                 "h2d_bytes_per_step": int(u0.nbytes), "d2h_bytes_per_step": int(out_host.numel() * 4)},
         "gpu_launches": launches,
         "clocks": clocks,
+        "energy_to_solution": energy,
     }
     ctx.close()
     if rank == 0:
