@@ -362,6 +362,16 @@ parareal_status parareal_diff_norms_noalloc(const double *a, const double *b, lo
                                             double *out5, void *cuda_stream);
 const char *parareal_noalloc_last_error(void);
 
+/* Failure-detection self-test.  Runs the bounded device-side wait of the
+ * tensor-core layers (the learned propagator's wait for MMA completion) on a
+ * barrier that nothing ever arrives on, in one single-warp kernel on
+ * `cuda_stream` (NULL = the legacy default stream), and synchronises it.
+ * Returns PARAREAL_E_TIMEOUT when the wait gave up as designed (after about
+ * 2^18 tries), PARAREAL_OK if it did not (a broken wait), PARAREAL_E_CUDA on
+ * a CUDA error.  Allocates one int of device memory for the flag.  The device
+ * stays usable afterwards.  No counterpart in the paper. */
+parareal_status parareal_selftest_timeout(void *cuda_stream);
+
 /* Number of kernel launches this context issued so far (for reporting). */
 long long parareal_launch_count(const parareal_ctx *ctx);
 

@@ -453,3 +453,22 @@ extern "C" parareal_status parareal_make_pairs(parareal_ctx *c, const float *ics
     return c->f64 ? make_pairs_t<double>(c, ics, n_ics, pairs_u, pairs_f, pair_slice)
                   : make_pairs_t<float>(c, ics, n_ics, pairs_u, pairs_f, pair_slice);
 }
+
+extern "C" parareal_status parareal_selftest_timeout(void *cuda_stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int *flag = nullptr;
+    if (cudaMalloc((void **)&flag, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, PARAREAL_E_NOMEM, "self-test flag allocation failed");
+    }
+    int h = -1;
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_wait_selftest(1ll << 18, flag, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(flag);
+    if (e != cudaSuccess) return fail(nullptr, PARAREAL_E_CUDA, std::string("self-test: ") + cudaGetErrorString(e));
+    if (h == 1) return fail(nullptr, PARAREAL_E_TIMEOUT, "bounded wait gave up as designed (self-test)");
+    return PARAREAL_OK;
+}

@@ -34,6 +34,9 @@ cudaError_t configure_net_kernels();
 // m a multiple of 16.  errflag (device int) is set if an MMA completion wait
 // runs out.
 cudaError_t configure_net_tc();
+// Self-test of the bounded completion wait of the tensor-core layers: waits
+// `limit` tries on an mbarrier nothing arrives on; *flag = 1 when it gave up.
+cudaError_t launch_wait_selftest(long long limit, int *flag, cudaStream_t st);
 bool net_tc_supported(int m);
 cudaError_t launch_net_mid_tc(const __nv_bfloat16 *in, int m, int batch, const __nv_bfloat16 *Bt,
                               const float *bias, __nv_bfloat16 *out, int lin, int *errflag,

@@ -93,9 +93,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity)
     return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity)
+// Waits for the phase of `parity` to complete, giving up (false) after
+// `limit` tries; the caller then records the failure and returns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity,
+                                                  long long limit = WAIT_LIMIT)
 {
-    for (long long i = 0; i < WAIT_LIMIT; ++i)
+    for (long long i = 0; i < limit; ++i)
         if (mbar_try_wait(mbar, parity)) return true;
     return false;
 }
@@ -281,6 +284,27 @@ cudaError_t launch_net_mid_tc(const bf16 *in, int m, int batch, const bf16 *Bt, 
     const long long cap = 152 * 3;      // three CTAs of 60 KB shared memory per SM
     const int grid = (int)(tiles < cap ? tiles : cap);
     net_mid_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(in, m, batch, Bt, bias, out, lin, errflag);
+    return cudaGetLastError();
+}
+
+// Failure-detection self-test: the bounded wait above on an mbarrier that
+// no thread ever arrives on.  The wait gives up after `limit` tries and the
+// kernel sets *flag; nothing else is touched, so the device stays usable.
+__global__ void wait_selftest_kernel(long long limit, int *flag)
+{
+    __shared__ __align__(8) unsigned long long mbar;
+    const uint32_t a = smem_addr(&mbar);
+    if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(a) : "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *flag = mbar_wait_bounded(a, 0u, limit) ? 0 : 1;
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(a) : "memory");
+    }
+}
+
+cudaError_t launch_wait_selftest(long long limit, int *flag, cudaStream_t st)
+{
+    wait_selftest_kernel<<<1, 32, 0, st>>>(limit, flag);
     return cudaGetLastError();
 }
 

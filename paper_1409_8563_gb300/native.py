@@ -110,6 +110,7 @@ SIGNATURES = {
     "parareal_profile": (_i, [_vp, _i]),
     "parareal_profile_read": (_i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]),
     "parareal_launch_count": (ctypes.c_longlong, [_vp]),
+    "parareal_selftest_timeout": (_i, [_vp]),
     "parareal_last_error": (_cp, [_vp]),
     "parareal_destroy": (None, [_vp]),
 }
@@ -153,6 +154,12 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def selftest_timeout(stream=None):
+    """Run the bounded device-side wait on a barrier nothing arrives on;
+    returns its status (E_TIMEOUT when the wait gave up as designed)."""
+    return int(lib().parareal_selftest_timeout(_stream_ptr(stream)))
 
 
 def stability(cfg):
