@@ -149,12 +149,17 @@ def test_plain_fp64_32_configuration_matches_oracle():
     ctx.close()
 
 
-def test_fp32_256_fine_sweep_full_size_against_modal_solution():
-    """Full 256^3, 32-slice batched fine sweep in the benchmark's launch shape:
-    U[2m+1] is set to the exact discrete F(U[2m]) (modal oracle), so the fine
-    residual of odd slices is the relative L2 error of the GPU sweep."""
+@pytest.mark.parametrize("shape", [(0, 64, 32, 256), (2, 64, 32, 256)])
+def test_fp32_256_fine_sweep_full_size_against_modal_solution(monkeypatch, shape):
+    """Full 256^3, 32-slice batched fine sweep in the launch shapes the
+    benchmark's autotuner chooses between (64 x 32 tiles, one or two rows per
+    thread, whole z columns): U[2m+1] is set to the exact discrete F(U[2m])
+    (modal oracle), so the fine residual of odd slices is the relative L2
+    error of the GPU sweep."""
+    tile_env(monkeypatch, fine=shape)
     cfg, _ = configs.fp32_256()
     ctx = native.Parareal(cfg)
+    assert ctx.launch_shape()[0] == shape
     nf, _ = steps(cfg)
     n = cfg.n
     nu = (cfg.nu0, cfg.nu_amp, cfg.nu_omega)
