@@ -362,6 +362,23 @@ parareal_status parareal_diff_norms_noalloc(const double *a, const double *b, lo
                                             double *out5, void *cuda_stream);
 const char *parareal_noalloc_last_error(void);
 
+/* Checkpoint and resume of the iteration state (a fault-tolerance aid; no
+ * counterpart in the paper).  parareal_save_state copies the iterate
+ * U^k[0..N] (FP64), the stored coarse outputs G(U^k[n]), the reference
+ * u_fine(T) if one is set, and the iteration count into a caller-owned host
+ * buffer of at least *needed bytes (host NULL: only report *needed).
+ * parareal_load_state restores such a buffer into a context created with the
+ * same configuration (grid, slices, coarsening, precision, kind of G); the
+ * next parareal_iterate then continues exactly, bitwise, where the saved
+ * context would have.  A learned propagator's weights are not part of the
+ * state (parareal_get/set_coarse_model); the per-slice changes reported by
+ * parareal_residual(DIFF_*) read zero until the next iteration.  Both calls
+ * synchronise the context stream.  Errors: PARAREAL_E_STATE (nothing to
+ * save), PARAREAL_E_INVALID (buffer too small, not a saved state, or another
+ * configuration). */
+parareal_status parareal_save_state(parareal_ctx *ctx, void *host, size_t bytes, size_t *needed);
+parareal_status parareal_load_state(parareal_ctx *ctx, const void *host, size_t bytes);
+
 /* Failure-detection self-test.  Runs the bounded device-side wait of the
  * tensor-core layers (the learned propagator's wait for MMA completion) on a
  * barrier that nothing ever arrives on, in one single-warp kernel on

@@ -779,6 +779,100 @@ extern "C" parareal_status parareal_set_slice(parareal_ctx *c, int slice, const 
     return load_field(c, c->U + (long long)slice * c->P, src, dtype, mem);
 }
 
+// ----------------------------------------------------------- checkpoint
+
+namespace {
+// Layout of a saved iteration state: this header, then U[0..N] (FP64), the
+// N stored coarse outputs G(U^k[n]), then u_fine(T) when a reference is set.
+struct StateHeader {
+    char magic[8];
+    int n, N, r, f64, g_fine, k_total, started, has_ref;
+    long long P, gbytes;
+};
+constexpr char STATE_MAGIC[8] = {'P', 'R', 'L', 'S', 'T', 'A', 'T', '1'};
+}  // namespace
+
+static bool alloc_ref(parareal_ctx *c)
+{
+    if (cudaMalloc((void **)&c->ref, (size_t)c->P * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->ref = nullptr;
+        return false;
+    }
+    return true;
+}
+
+static size_t gold_bytes(const parareal_ctx *c)
+{
+    return c->g_fine ? (size_t)c->P * sizeof(double) : (size_t)c->Pc * c->esz;
+}
+
+static size_t state_bytes(const parareal_ctx *c)
+{
+    return sizeof(StateHeader) + (size_t)(c->N + 1) * c->P * sizeof(double) +
+           (size_t)c->N * gold_bytes(c) + (c->has_ref ? (size_t)c->P * sizeof(double) : 0);
+}
+
+extern "C" parareal_status parareal_save_state(parareal_ctx *c, void *host, size_t bytes, size_t *needed)
+{
+    if (!c) return PARAREAL_E_INVALID;
+    const size_t need = state_bytes(c);
+    if (needed) *needed = need;
+    if (!host) return PARAREAL_OK;
+    if (!c->has_problem) return fail(c, PARAREAL_E_STATE, "no problem set: nothing to save");
+    if (bytes < need) return fail(c, PARAREAL_E_INVALID, "state buffer smaller than parareal_save_state's size");
+    StateHeader h{};
+    std::memcpy(h.magic, STATE_MAGIC, sizeof h.magic);
+    h.n = c->n; h.N = c->N; h.r = c->r; h.f64 = c->f64; h.g_fine = c->g_fine;
+    h.k_total = c->k_total; h.started = c->started; h.has_ref = c->has_ref;
+    h.P = c->P; h.gbytes = (long long)gold_bytes(c);
+    char *p = static_cast<char *>(host);
+    std::memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    const size_t ub = (size_t)(c->N + 1) * c->P * sizeof(double);
+    CK(cudaMemcpyAsync(p, c->U, ub, cudaMemcpyDeviceToHost, c->st));
+    p += ub;
+    for (int i = 1; i <= c->N; ++i, p += gold_bytes(c))
+        CK(cudaMemcpyAsync(p, c->gold[i], gold_bytes(c), cudaMemcpyDeviceToHost, c->st));
+    if (c->has_ref) CK(cudaMemcpyAsync(p, c->ref, (size_t)c->P * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return PARAREAL_OK;
+}
+
+extern "C" parareal_status parareal_load_state(parareal_ctx *c, const void *host, size_t bytes)
+{
+    if (!c) return PARAREAL_E_INVALID;
+    if (!host || bytes < sizeof(StateHeader)) return fail(c, PARAREAL_E_INVALID, "state buffer too small");
+    StateHeader h;
+    std::memcpy(&h, host, sizeof h);
+    if (std::memcmp(h.magic, STATE_MAGIC, sizeof h.magic) != 0)
+        return fail(c, PARAREAL_E_INVALID, "not a saved Parareal state");
+    if (h.n != c->n || h.N != c->N || h.r != c->r || h.f64 != (int)c->f64 || h.g_fine != (int)c->g_fine ||
+        h.P != c->P || h.gbytes != (long long)gold_bytes(c))
+        return fail(c, PARAREAL_E_INVALID, "saved state belongs to a different configuration");
+    if (h.has_ref && !c->ref && !alloc_ref(c)) return fail(c, PARAREAL_E_NOMEM, "reference allocation failed");
+    const bool had_ref = c->has_ref;
+    c->has_ref = h.has_ref != 0;
+    if (bytes < state_bytes(c)) {
+        c->has_ref = had_ref;
+        return fail(c, PARAREAL_E_INVALID, "state buffer shorter than its header says");
+    }
+    const char *p = static_cast<const char *>(host) + sizeof h;
+    const size_t ub = (size_t)(c->N + 1) * c->P * sizeof(double);
+    CK(cudaMemcpyAsync(c->U, p, ub, cudaMemcpyHostToDevice, c->st));
+    p += ub;
+    for (int i = 1; i <= c->N; ++i, p += gold_bytes(c))
+        CK(cudaMemcpyAsync(c->gold[i], p, gold_bytes(c), cudaMemcpyHostToDevice, c->st));
+    if (c->has_ref) CK(cudaMemcpyAsync(c->ref, p, (size_t)c->P * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->k_total = h.k_total;
+    c->started = h.started != 0;
+    c->has_problem = true;
+    std::fill(c->diff_inf.begin(), c->diff_inf.end(), 0.0);
+    std::fill(c->diff_l2.begin(), c->diff_l2.end(), 0.0);
+    return PARAREAL_OK;
+}
+
 extern "C" parareal_status parareal_fine_sweep(parareal_ctx *c, int first, int count)
 {
     if (!c) return PARAREAL_E_INVALID;

@@ -111,6 +111,8 @@ SIGNATURES = {
     "parareal_profile_read": (_i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]),
     "parareal_launch_count": (ctypes.c_longlong, [_vp]),
     "parareal_selftest_timeout": (_i, [_vp]),
+    "parareal_save_state": (_i, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "parareal_load_state": (_i, [_vp, _vp, ctypes.c_size_t]),
     "parareal_last_error": (_cp, [_vp]),
     "parareal_destroy": (None, [_vp]),
 }
@@ -278,6 +280,19 @@ class Parareal:
                                                      ctypes.c_void_p(grad_out.data_ptr()),
                                                      ctypes.byref(loss)))
         return loss.value
+
+    def save_state(self):
+        """The iteration state as a bytes-like numpy uint8 array (host)."""
+        need = ctypes.c_size_t()
+        self._check(lib().parareal_save_state(self._h, None, 0, ctypes.byref(need)))
+        buf = np.empty(need.value, dtype=np.uint8)
+        self._check(lib().parareal_save_state(self._h, ctypes.c_void_p(buf.ctypes.data), buf.nbytes,
+                                              ctypes.byref(need)))
+        return buf
+
+    def load_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        return self._check(lib().parareal_load_state(self._h, ctypes.c_void_p(buf.ctypes.data), buf.nbytes))
 
     def autotune(self, cache_path=None):
         """Time the launch shapes and keep the fastest (call before set_problem)."""
