@@ -788,8 +788,29 @@ struct StateHeader {
     char magic[8];
     int n, N, r, f64, g_fine, k_total, started, has_ref;
     long long P, gbytes;
+    unsigned long long cfg_hash;   // fingerprint of every config field the iteration depends on
 };
-constexpr char STATE_MAGIC[8] = {'P', 'R', 'L', 'S', 'T', 'A', 'T', '1'};
+constexpr char STATE_MAGIC[8] = {'P', 'R', 'L', 'S', 'T', 'A', 'T', '2'};
+
+// FNV-1a over the bytes of one value.
+template <typename V>
+void fnv(unsigned long long &h, const V &v)
+{
+    const unsigned char *b = reinterpret_cast<const unsigned char *>(&v);
+    for (size_t i = 0; i < sizeof(V); ++i) h = (h ^ b[i]) * 1099511628211ull;
+}
+
+unsigned long long config_hash(const parareal_config &c)
+{
+    unsigned long long h = 1469598103934665603ull;
+    fnv(h, c.n); fnv(h, c.n_slices); fnv(h, c.T); fnv(h, c.dt_fine); fnv(h, c.dt_coarse);
+    fnv(h, c.coarse_factor);
+    for (int d = 0; d < 3; ++d) fnv(h, c.a[d]);
+    fnv(h, c.nu0); fnv(h, c.nu_amp); fnv(h, c.nu_omega); fnv(h, c.fine_dtype); fnv(h, c.nu_mode);
+    fnv(h, c.coarse_kind); fnv(h, c.learned_skip); fnv(h, c.fine_scheme); fnv(h, c.learned_act);
+    fnv(h, c.correction_form); fnv(h, c.learned_eval);
+    return h;
+}
 }  // namespace
 
 static bool alloc_ref(parareal_ctx *c)
@@ -826,6 +847,7 @@ extern "C" parareal_status parareal_save_state(parareal_ctx *c, void *host, size
     h.n = c->n; h.N = c->N; h.r = c->r; h.f64 = c->f64; h.g_fine = c->g_fine;
     h.k_total = c->k_total; h.started = c->started; h.has_ref = c->has_ref;
     h.P = c->P; h.gbytes = (long long)gold_bytes(c);
+    h.cfg_hash = config_hash(c->cfg);
     char *p = static_cast<char *>(host);
     std::memcpy(p, &h, sizeof h);
     p += sizeof h;
@@ -848,7 +870,7 @@ extern "C" parareal_status parareal_load_state(parareal_ctx *c, const void *host
     if (std::memcmp(h.magic, STATE_MAGIC, sizeof h.magic) != 0)
         return fail(c, PARAREAL_E_INVALID, "not a saved Parareal state");
     if (h.n != c->n || h.N != c->N || h.r != c->r || h.f64 != (int)c->f64 || h.g_fine != (int)c->g_fine ||
-        h.P != c->P || h.gbytes != (long long)gold_bytes(c))
+        h.P != c->P || h.gbytes != (long long)gold_bytes(c) || h.cfg_hash != config_hash(c->cfg))
         return fail(c, PARAREAL_E_INVALID, "saved state belongs to a different configuration");
     if (h.has_ref && !c->ref && !alloc_ref(c)) return fail(c, PARAREAL_E_NOMEM, "reference allocation failed");
     const bool had_ref = c->has_ref;

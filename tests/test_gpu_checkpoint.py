@@ -63,6 +63,14 @@ def test_foreign_or_truncated_states_are_rejected():
     with pytest.raises(native.PararealError) as e:
         a.load_state(bad)
     assert e.value.status == native.E_INVALID
+    # same sizes, another viscosity history nu(t): a different configuration
+    visc, _ = configs.small(n=16, n_slices=3, dtype=native.F32, r=2, nf=8, nc=2)
+    visc.nu_omega = 2.0 * visc.nu_omega
+    c = native.Parareal(visc)
+    with pytest.raises(native.PararealError) as e:
+        c.load_state(state)
+    assert e.value.status == native.E_INVALID
+    c.close()
     a.load_state(state)                      # the context stays usable
     k, _ = a.iterate(1, 0.0, native.STOP_NONE)
     assert k == 1
