@@ -777,11 +777,16 @@ def main():
                     help="fine_sweep: launch shape 'tx,ty,zchunk' (fused kernel, one row per "
                          "thread) or 'path,tx,ty,zchunk' (path 2: two rows per thread) instead of "
                          "autotuning")
-    ap.add_argument("--n-ics", type=int, default=63)
-    ap.add_argument("--epochs", type=int, default=10)
+    ap.add_argument("--n-ics", type=int, default=None,
+                    help="learned workloads: seeded training fields (default 63 at 128^3, 2 at 512^3)")
+    ap.add_argument("--epochs", type=int, default=None, help="default 10 at 128^3, 16 at 512^3")
     ap.add_argument("--batch", type=int, default=8)
-    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr", type=float, default=None, help="default 1e-3 at 128^3, 2e-3 at 512^3")
     args = ap.parse_args()
+    big = args.workload == "learned_512"
+    args.n_ics = args.n_ics if args.n_ics is not None else (2 if big else 63)
+    args.epochs = args.epochs if args.epochs is not None else (16 if big else 10)
+    args.lr = args.lr if args.lr is not None else (2e-3 if big else 1e-3)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "fp64_32":
