@@ -371,11 +371,14 @@ const char *parareal_noalloc_last_error(void);
  * same configuration (grid, slices, coarsening, precision, kind of G); the
  * next parareal_iterate then continues exactly, bitwise, where the saved
  * context would have.  A learned propagator's weights are not part of the
- * state (parareal_get/set_coarse_model); the per-slice changes reported by
+ * state (parareal_get/set_coarse_model), but a fingerprint of them is: with
+ * a learned G, saving and loading need a model, and a state saved with other
+ * weights is refused.  The per-slice changes reported by
  * parareal_residual(DIFF_*) read zero until the next iteration.  Both calls
  * synchronise the context stream.  Errors: PARAREAL_E_STATE (nothing to
- * save), PARAREAL_E_INVALID (buffer too small, not a saved state, or another
- * configuration). */
+ * save; learned G without a model, or with other weights than the saved
+ * state's), PARAREAL_E_INVALID (buffer too small, not a saved state, or
+ * another configuration). */
 parareal_status parareal_save_state(parareal_ctx *ctx, void *host, size_t bytes, size_t *needed);
 parareal_status parareal_load_state(parareal_ctx *ctx, const void *host, size_t bytes);
 

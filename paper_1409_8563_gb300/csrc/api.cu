@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "ctx.cuh"
+#include "net.cuh"
 
 using namespace pr;
 
@@ -176,7 +177,7 @@ static void default_tiles(int dtype, int n, int count, int *path, int *tx, int *
     if (*tx == 0) { *path = PATH_STAGED; *tx = 16; *ty = 8; }
     // z chunk: whole columns unless the launch would leave SMs idle
     int z = n;
-    while (z > 16 && (long long)count * (n / *tx) * (n / *ty) * ((n + z - 1) / z) < 2 * 152) z /= 2;
+    while (z > 16 && (long long)count * (n / *tx) * (n / *ty) * ((n + z - 1) / z) < 2ll * sm_count()) z /= 2;
     *zc = z;
 }
 
@@ -789,8 +790,9 @@ struct StateHeader {
     int n, N, r, f64, g_fine, k_total, started, has_ref;
     long long P, gbytes;
     unsigned long long cfg_hash;   // fingerprint of every config field the iteration depends on
+    unsigned long long model_hash; // learned G: fingerprint of its FP32 master weights (else 0)
 };
-constexpr char STATE_MAGIC[8] = {'P', 'R', 'L', 'S', 'T', 'A', 'T', '2'};
+constexpr char STATE_MAGIC[8] = {'P', 'R', 'L', 'S', 'T', 'A', 'T', '3'};
 
 // FNV-1a over the bytes of one value.
 template <typename V>
@@ -812,6 +814,24 @@ unsigned long long config_hash(const parareal_config &c)
     return h;
 }
 }  // namespace
+
+// Fingerprint of the learned propagator's weights (0 for the other coarse
+// propagators).  A learned context without a model gives E_STATE.
+static parareal_status model_hash(parareal_ctx *c, unsigned long long *h)
+{
+    *h = 0;
+    const int k = c->cfg.coarse_kind;
+    if (k != PARAREAL_COARSE_LEARNED) return PARAREAL_OK;
+    if (!c->net.has_model || !c->net.master)
+        return fail(c, PARAREAL_E_STATE, "learned coarse propagator has no model: set or train one first");
+    std::vector<float> w(NET_PARAMS);
+    CK(cudaMemcpyAsync(w.data(), c->net.master, NET_PARAMS * sizeof(float), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    unsigned long long v = 1469598103934665603ull;
+    for (float x : w) fnv(v, x);
+    *h = v | 1ull;     // never 0 for a learned model
+    return PARAREAL_OK;
+}
 
 static bool alloc_ref(parareal_ctx *c)
 {
@@ -848,6 +868,8 @@ extern "C" parareal_status parareal_save_state(parareal_ctx *c, void *host, size
     h.k_total = c->k_total; h.started = c->started; h.has_ref = c->has_ref;
     h.P = c->P; h.gbytes = (long long)gold_bytes(c);
     h.cfg_hash = config_hash(c->cfg);
+    parareal_status ms = model_hash(c, &h.model_hash);
+    if (ms != PARAREAL_OK) return ms;
     char *p = static_cast<char *>(host);
     std::memcpy(p, &h, sizeof h);
     p += sizeof h;
@@ -872,6 +894,11 @@ extern "C" parareal_status parareal_load_state(parareal_ctx *c, const void *host
     if (h.n != c->n || h.N != c->N || h.r != c->r || h.f64 != (int)c->f64 || h.g_fine != (int)c->g_fine ||
         h.P != c->P || h.gbytes != (long long)gold_bytes(c) || h.cfg_hash != config_hash(c->cfg))
         return fail(c, PARAREAL_E_INVALID, "saved state belongs to a different configuration");
+    unsigned long long mh = 0;
+    parareal_status ms = model_hash(c, &mh);
+    if (ms != PARAREAL_OK) return ms;
+    if (mh != h.model_hash)
+        return fail(c, PARAREAL_E_STATE, "saved state was iterated with other coarse-model weights");
     if (h.has_ref && !c->ref && !alloc_ref(c)) return fail(c, PARAREAL_E_NOMEM, "reference allocation failed");
     const bool had_ref = c->has_ref;
     c->has_ref = h.has_ref != 0;

@@ -160,7 +160,7 @@ correct_kernel(const TF *__restrict__ Fv, const TG *__restrict__ gnew, const TG 
 int correct_blocks(long long P)
 {
     long long b = (P + RED_THREADS - 1) / RED_THREADS;
-    const long long cap = 152 * 8;
+    const long long cap = 8ll * sm_count();
     return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 

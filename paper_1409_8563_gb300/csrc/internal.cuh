@@ -87,6 +87,9 @@ __host__ __device__ inline void op_weights(int op, double nu, double dt, int n, 
     }
 }
 
+// Streaming multiprocessors of the current device (cached per device).
+int sm_count();
+
 // ------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return cudaGetLastError().
 
@@ -97,6 +100,7 @@ cudaError_t launch_rk4_fused(const StepArgs &a, const T *in, T *out, int tile_x,
                              int zchunk, int rows, cudaStream_t st);
 bool rk4_fused_supported(int dtype, int n, int tile_x, int tile_y, int rows);
 cudaError_t configure_rk4_kernels();
+
 
 // One RK4 stage per launch (no halo recomputation; state kept in HBM/L2),
 // any operator.  Stage 0 is one forward Euler step: ydst = ysrc + dt A ysrc

@@ -113,7 +113,11 @@ parareal_status net_check(parareal_ctx *c)
     int h = 0;
     CK(cudaMemcpyAsync(&h, S.tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
-    if (h) return fail(c, PARAREAL_E_TIMEOUT, "tensor-core completion wait ran out in the learned propagator");
+    if (h) {
+        // clear the flag so that later calls on this context report only their own timeouts
+        CK(cudaMemsetAsync(S.tc_err, 0, sizeof(int), c->st));
+        return fail(c, PARAREAL_E_TIMEOUT, "tensor-core completion wait ran out in the learned propagator");
+    }
     return PARAREAL_OK;
 }
 

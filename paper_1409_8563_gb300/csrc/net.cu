@@ -733,7 +733,8 @@ cudaError_t launch_net_mid(int mode, const bf16 *in, int m, int batch, const bf1
 int net_partial_blocks(int m, int batch)
 {
     const long long t = (long long)tiles_of(m) * batch;
-    return (int)(t < 152 * 4 ? t : 152 * 4);
+    const long long cap = 4ll * sm_count();
+    return (int)(t < cap ? t : cap);
 }
 
 cudaError_t launch_net_mid_wgrad(const bf16 *x, const bf16 *dz, int m, int batch, float *partials,

@@ -225,9 +225,15 @@ net_mid_tc(const bf16 *__restrict__ in, int m, int batch, const bf16 *__restrict
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
                          ::"r"(mbar_a) : "memory");
         }
-        if (!mbar_wait_bounded(mbar_a, parity)) {
+        // every thread waits (bounded) for the MMAs, then the block takes one
+        // decision: if any thread gave up, all leave the tile loop together,
+        // so no warp-collective tensor-memory load or barrier below runs with
+        // part of the block gone.  After a give-up the block waits once more
+        // (bounded, again block-wide) for the MMAs in flight before the
+        // tensor memory they write is freed.
+        if (__syncthreads_or(mbar_wait_bounded(mbar_a, parity) ? 0 : 1)) {
             if (tid == 0) atomicExch(errflag, 1);
-            mbar_wait_bounded(mbar_a, parity);
+            (void)__syncthreads_or(mbar_wait_bounded(mbar_a, parity) ? 0 : 1);
             break;
         }
         parity ^= 1u;
@@ -281,7 +287,7 @@ cudaError_t launch_net_mid_tc(const bf16 *in, int m, int batch, const bf16 *Bt, 
                               bf16 *out, int lin, int *errflag, cudaStream_t st)
 {
     const long long tiles = (long long)(m / 8) * (m / 16) * (m / ZB) * batch;
-    const long long cap = 152 * 3;      // three CTAs of 60 KB shared memory per SM
+    const long long cap = 3ll * sm_count();   // three CTAs of 60 KB shared memory per SM
     const int grid = (int)(tiles < cap ? tiles : cap);
     net_mid_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(in, m, batch, Bt, bias, out, lin, errflag);
     return cudaGetLastError();

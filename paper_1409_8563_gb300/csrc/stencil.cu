@@ -668,7 +668,21 @@ __global__ void convert_f2d_kernel(const float *__restrict__ s, double *__restri
 static unsigned grid_for(long long N)
 {
     long long b = (N + 255) / 256;
-    return (unsigned)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+    const long long cap = 16ll * sm_count();
+    return (unsigned)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
+int sm_count()
+{
+    // per device, queried once (device ordinals beyond the table are queried each time)
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    if (dev >= 0 && dev < 64 && cache[dev] > 0) return cache[dev];
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    if (dev >= 0 && dev < 64) cache[dev] = n;
+    return n;
 }
 
 cudaError_t launch_convert_f64_to_f32(const double *src, float *dst, long long N, cudaStream_t st)

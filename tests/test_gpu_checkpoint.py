@@ -76,3 +76,39 @@ def test_foreign_or_truncated_states_are_rejected():
     assert k == 1
     a.close()
     b.close()
+
+
+def test_learned_state_needs_the_weights_it_was_iterated_with():
+    """The coarse model's weights are not saved, but their fingerprint is: a
+    learned context without a model cannot save or load, and a state iterated
+    with other weights is refused."""
+    from paper_1409_8563_gb300 import inputs
+    cfg, u0 = configs.small(n=16, n_slices=3, dtype=native.F32, nf=8, nc=2)
+    cfg.coarse_kind = native.COARSE_LEARNED
+    w = inputs.initial_weights(seed=1)
+    a = native.Parareal(cfg)
+    a.set_problem(torch.from_numpy(u0).cuda())
+    with pytest.raises(native.PararealError) as e:
+        a.save_state()                       # no model yet
+    assert e.value.status == native.E_STATE
+    a.set_coarse_model(w)
+    a.iterate(1, 0.0, native.STOP_NONE)
+    state = a.save_state()
+    b = native.Parareal(cfg)
+    with pytest.raises(native.PararealError) as e:
+        b.load_state(state)                  # no model
+    assert e.value.status == native.E_STATE
+    w2 = w.copy()
+    w2[-1] += 1e-3                           # another model
+    b.set_coarse_model(w2)
+    with pytest.raises(native.PararealError) as e:
+        b.load_state(state)
+    assert e.value.status == native.E_STATE
+    b.set_coarse_model(w)                    # the same weights: accepted, continues bitwise
+    b.load_state(state)
+    ka, ha = a.iterate(1, 0.0, native.STOP_NONE)
+    kb, hb = b.iterate(1, 0.0, native.STOP_NONE)
+    assert ka == kb == 1 and np.array_equal(ha[:, :3], hb[:, :3])
+    assert np.array_equal(read_all(a, cfg)[-1], read_all(b, cfg)[-1])
+    a.close()
+    b.close()
