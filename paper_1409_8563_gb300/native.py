@@ -62,6 +62,7 @@ class Config(ctypes.Structure):
 
 
 MODEL_PARAMS = 15169
+NOALLOC_MAX_COUNT = 1 << 26     # PARAREAL_NOALLOC_MAX_COUNT
 
 
 class TrainConfig(ctypes.Structure):

@@ -133,3 +133,84 @@ def test_linear_network_equals_its_composed_kernel():
         K = net.compose_linear(params, nu_hat)
         got = su + net.apply_kernel(su, K)
         assert np.max(np.abs(got - g)) <= 1e-12 * np.max(np.abs(g)), np.max(np.abs(got - g))
+
+
+@pytest.mark.parametrize("b1,b2,want", [(0.5, 0.5, 1.0 / np.sqrt(3.0)),
+                                         (0.5, 0.75, np.sqrt(7.0 / 27.0)),
+                                         (0.9, 0.999, (0.9 / 1.9) * np.sqrt(1.999 / 0.999))])
+def test_second_adam_step_closed_form(b1, b2, want):
+    """Two Adam steps with gradients g, then 0.  Unrolling the moment
+    recurrences with their bias corrections gives, at step 2,
+    m_hat = b1 g / (1 + b1) and v_hat = b2 g^2 / (1 + b2), so the second step
+    moves the parameter by lr (b1 / (1 + b1)) sqrt((1 + b2) / b2) sign(g).
+    A swapped decay, a wrong bias-correction exponent or a missing square
+    root changes it."""
+    lr = 0.01
+    for g in (3.0, -0.25):
+        params = [[np.array([[1.0]]), np.array([0.0])]]
+        m = net.zeros_like_params(params)
+        v = net.zeros_like_params(params)
+        net.adam_step(params, [[np.array([[g]]), np.array([1.0])]], m, v, 1, lr=lr, b1=b1, b2=b2,
+                      eps=0.0)
+        p1 = params[0][0][0, 0]
+        assert abs(p1 - (1.0 - lr * np.sign(g))) < 1e-15
+        net.adam_step(params, [[np.array([[0.0]]), np.array([1.0])]], m, v, 2, lr=lr, b1=b1, b2=b2,
+                      eps=0.0)
+        step = p1 - params[0][0][0, 0]
+        assert abs(step - lr * want * np.sign(g)) < 1e-14, (step, lr * want)
+
+
+def test_constant_gradient_adam_steps_by_lr():
+    """With a constant gradient the bias-corrected moments are exactly g and
+    g^2 at every step, so each step is lr sign(g)."""
+    params = [[np.array([[0.0, 0.0]]), np.array([0.0])]]
+    m = net.zeros_like_params(params)
+    v = net.zeros_like_params(params)
+    g = [[np.array([[0.7, -5.0]]), np.array([1.0])]]
+    for step in range(1, 6):
+        net.adam_step(params, g, m, v, step, lr=0.1, eps=0.0)
+        assert np.allclose(params[0][0], [[-0.1 * step, 0.1 * step]], atol=1e-12, rtol=0)
+
+
+def _one_path_params(a, c1, b, c, d, e, a_nu=0.0):
+    """Network whose only nonzero path is channel 0 through the centre taps:
+    layer 1 weight a on input channel 0 (a_nu on channel 1) and bias c1,
+    layers 2 and 3 weights b and c, layer 4 weight d and bias e."""
+    params = [[np.zeros((co, ci, 3, 3, 3)), np.zeros(co)] for ci, co in net.LAYERS]
+    params[0][0][0, 0, 1, 1, 1] = a
+    params[0][0][0, 1, 1, 1, 1] = a_nu
+    params[0][1][0] = c1
+    params[1][0][0, 0, 1, 1, 1] = b
+    params[2][0][0, 0, 1, 1, 1] = c
+    params[3][0][0, 0, 1, 1, 1] = d
+    params[3][1][0] = e
+    return params
+
+
+def test_gelu_follows_the_first_three_layers_only():
+    """G(u) = S(u) + d gelu(c gelu(b gelu(a S(u) + c1))) + e, written out with
+    the error function: GELU after layers 1-3 and none after layer 4.  An
+    activation moved, added or dropped changes the value."""
+    import math
+    u, _ = small_problem(n=4, seed=5)
+    shift = (1, 0, 2)
+    a, c1, b, c, d, e = 1.3, 0.2, -0.8, 1.7, 0.9, -0.05
+    out, _ = net.forward(u, 0.6, _one_path_params(a, c1, b, c, d, e), shift)
+    gelu = np.vectorize(lambda x: 0.5 * x * (1.0 + math.erf(x / math.sqrt(2.0))))
+    su = core.shift(u, shift)
+    want = su + d * gelu(c * gelu(b * gelu(a * su + c1))) + e
+    assert np.allclose(out, want, atol=1e-13, rtol=0)
+    # GELU after layer 4 as well would give a different value
+    assert np.max(np.abs(out - (su + gelu(d * gelu(c * gelu(b * gelu(a * su + c1))) + e)))) > 1e-3
+
+
+def test_linear_mode_is_the_product_of_the_path_weights():
+    """Linear mode: identity activations, biases unused, second input channel
+    nu_hat S(u): G(u) = S(u) + d c b (a + a_nu nu_hat) S(u)."""
+    u, _ = small_problem(n=4, seed=6)
+    shift = (0, 1, 1)
+    a, a_nu, b, c, d, nu_hat = 0.7, -0.4, 1.1, -0.6, 0.5, 0.8
+    out, _ = net.forward(u, nu_hat, _one_path_params(a, 0.3, b, c, d, 0.2, a_nu=a_nu), shift,
+                         linear=True)
+    su = core.shift(u, shift)
+    assert np.allclose(out, su * (1.0 + d * c * b * (a + a_nu * nu_hat)), atol=1e-14, rtol=0)

@@ -57,3 +57,47 @@ def test_noalloc_rejects_counts_beyond_its_scratch():
     st = noalloc(a, a, out, count=(1 << 26) + 1)   # rejected on the host, nothing launched
     assert st == native.E_INVALID
     assert b"exceeds the maximum" in native.lib().parareal_noalloc_last_error()
+
+
+def _check_against_numpy(a, b, o):
+    d = a - b
+    assert o[0] == np.max(np.abs(d)) and o[1] == np.max(np.abs(b))
+    assert abs(o[2] - np.sum(d * d)) <= 1e-11 * np.sum(d * d)
+    assert abs(o[3] - np.sum(b * b)) <= 1e-11 * np.sum(b * b)
+    assert o[4] == 0.0
+
+
+@pytest.mark.parametrize("count", [1_000_003, native.NOALLOC_MAX_COUNT - 3])
+def test_noalloc_ragged_and_near_maximal_counts(count):
+    """A count that is not a multiple of the per-block chunk, and one that
+    fills the scratch array up to its last block (about 0.5 GB of FP64 per
+    input), on two calls in a row with different data."""
+    rng = np.random.default_rng(count % 1000)
+    out = torch.full((5,), -1.0, dtype=torch.float64, device="cuda")
+    for call in range(2):
+        a = rng.standard_normal(count)
+        b = rng.standard_normal(count) * (call + 1)
+        assert noalloc(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), out) == native.OK
+        torch.cuda.synchronize()
+        _check_against_numpy(a, b, out.cpu().numpy())
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_noalloc_flags_a_non_finite_value(bad):
+    count = 1_000_003
+    rng = np.random.default_rng(7)
+    a = rng.standard_normal(count)
+    b = rng.standard_normal(count)
+    a[count // 3] = bad
+    out = torch.zeros(5, dtype=torch.float64, device="cuda")
+    assert noalloc(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), out) == native.OK
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    assert o[4] == 1.0
+    assert not np.isfinite(o[0]) and not np.isfinite(o[2])
+    assert o[1] == np.max(np.abs(b)) and abs(o[3] - np.sum(b * b)) <= 1e-11 * np.sum(b * b)
+    # a later call on finite data clears the flag (the scratch keeps no state)
+    a[count // 3] = 0.0
+    assert noalloc(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), out) == native.OK
+    torch.cuda.synchronize()
+    _check_against_numpy(a, b, out.cpu().numpy())
