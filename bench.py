@@ -167,6 +167,50 @@ def sum_over_ranks(dist, x):
     return float(t.item())
 
 
+# FP32 instructions of one RK4 point-step of the fused kernel's arithmetic,
+# halo excluded: four 7-term stencil FMA chains, y4 = u + 2 h, and the step's
+# base b = u + ((y2 - u) + 2 (y3 - u) + (y4 - u)) / 3 (three subtractions, one
+# addition, two FMAs).
+FP32_OPS_PER_POINT_STEP = 4 * 7 + 1 + 6
+FP32_LANES_PER_SM = 128        # four sub-partitions of 32 FP32 lanes
+
+
+def alu_roof(point_steps_per_s, clocks):
+    """The fused step against the FP32 issue rate: one FP32 instruction per
+    lane per clock at the maximum SM clock (an FMA counts once)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = sms * FP32_LANES_PER_SM * mhz * 1e6
+    ach = point_steps_per_s * FP32_OPS_PER_POINT_STEP
+    return {"achieved": ach / 1e12, "peak": peak / 1e12, "unit": "T FP32 instr/s",
+            "frac": ach / peak, "ops_per_point_step": FP32_OPS_PER_POINT_STEP,
+            "peak_from": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz"}
+
+
+def s_bound(n_p, k, nc_over_nf, tauc_over_tauf):
+    """Speedup bound of Eq. (speedup): 1 / ((1 + K/N_p) (N_c/N_f)(tau_c/tau_f) + K/N_p)."""
+    return 1.0 / ((1.0 + k / n_p) * nc_over_nf * tauc_over_tauf + k / n_p)
+
+
+def gamma_terms(n_p, k, n_f, n_c, tau_f_serial, tau_f_batched, tau_c, t_p, t_s):
+    """Energy overhead models (Sec. 2.2.3).  gamma_bound = N_p / S_bound with
+    the paper's speedup bound (one node per slice), from the step costs
+    measured here.  On one GPU all slices share the device, so the same cost
+    model is also evaluated for one device at constant power: the start-up
+    chain and every iteration's serial G chain (Eq. cost_parareal's coarse
+    terms, one G per open slice), the batched fine sweeps of the open slices
+    at the batched per-slice step cost, over N_p N_f serial fine steps."""
+    sb = s_bound(n_p, k, n_c / n_f, tau_c / tau_f_serial)
+    coarse = (n_p + sum(n_p - j - 1 for j in range(k))) * n_c * tau_c
+    fine = sum(n_p - j for j in range(k)) * n_f * tau_f_batched
+    return {"gamma_bound_paper": n_p / sb, "s_bound_paper": sb,
+            "gamma_bound_one_gpu": (coarse + fine) / (n_p * n_f * tau_f_serial),
+            "t_ratio_measured": t_p / t_s,
+            "tau_f_serial_us": tau_f_serial * 1e6, "tau_f_batched_us": tau_f_batched * 1e6,
+            "tau_c_us": tau_c * 1e6, "K": k, "N_p": n_p, "N_f": n_f, "N_c": n_c}
+
+
 # ------------------------------------------------------------ CPU oracle leg
 
 def oracle_sample(n_steps, n=256):
@@ -308,6 +352,20 @@ def run(args):
             ev1.record(stream)
         ev1.synchronize()
     serial_rep_ms = ev0.elapsed_time(ev1) / reps
+    # one application of the coarse propagator alone (restriction, N_c coarse
+    # steps, prolongation), for the energy model's coarse step cost
+    g_src = u0_dev.float()
+    g_dst = torch.empty_like(g_src)
+    torch.cuda.synchronize()
+    ctx.propagate(1, g_src, g_dst, 1, 1)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(10):
+            ctx.propagate(1, g_src, g_dst, 1, 1)
+        ev1.record(stream)
+    ev1.synchronize()
+    g_apply_ms = ev0.elapsed_time(ev1) / 10
+    del g_src, g_dst
     total_ms = max_over_ranks(dist, sum(step_ms))
     updates = sum_over_ranks(dist, updates)
     value = updates / (total_ms / 1000.0) / 1e9
@@ -329,7 +387,12 @@ def run(args):
     avg_launch_ms = fine_ms / max(fine_launches, 1)
     bytes_per_launch = fine_bytes / max(fine_launches, 1)
     achieved = bytes_per_launch / (avg_launch_ms / 1000.0) / 1e9
+    # ncu DRAM traffic of a full N-field launch, scaled to the average launch
+    # of the solve (traffic grows in proportion to the fields per launch)
     traffic = ncu_traffic(fine_shape[0]) if args.workload == "fp32_256" else None
+    fields_per_launch = bytes_per_launch / (2.0 * 4.0 * P)
+    if traffic is not None:
+        traffic *= fields_per_launch / N
     k_star = max(len(h) for h in hists)
     final_defect = float(hists[-1][-1, 2])
 
@@ -348,11 +411,19 @@ def run(args):
     if p_par is not None and p_ser is not None:
         e_par = p_par * total_ms / args.steps / 1000.0
         e_ser = p_ser * serial_rep_ms / 1000.0
+        n_c = round(cfg.T / N / cfg.dt_coarse)
+        gam = gamma_terms(N, k_star, nf, n_c, serial_ms / 1000.0 / (N * nf),
+                          avg_launch_ms / 1000.0 / fields_per_launch,
+                          g_apply_ms / 1000.0 / n_c, total_ms / args.steps, serial_ms)
         energy = {"parareal_j": e_par, "serial_fine_j": e_ser, "ratio": e_par / e_ser,
+                  "gamma_measured": e_par / e_ser, **gam,
                   "power_w_parareal": p_par, "power_w_serial_fine": p_ser,
                   "what": "GPU board power (nvidia-smi, every 200 ms) x CUDA-event time per "
-                          "solve; the paper's node, network and cooling terms are not "
-                          "measurable here"}
+                          "solve; gamma_measured = Q_p / Q_s (Sec. 3.4.2); gamma_bound_paper = "
+                          "N_p / S_bound (Eq. gamma_expected) for one node per slice; "
+                          "gamma_bound_one_gpu = the same cost model for all slices on one GPU "
+                          "at constant power; the paper's node, network and cooling terms are "
+                          "not measurable here"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -372,8 +443,10 @@ def run(args):
         "roofline": {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "fields_per_launch": fields_per_launch,
                      "avg_launch_ms": avg_launch_ms, "timed_launches": fine_launches,
-                     "kernel_glups": bytes_per_launch / 8.0 / (avg_launch_ms / 1000.0) / 1e9},
+                     "kernel_glups": bytes_per_launch / 8.0 / (avg_launch_ms / 1000.0) / 1e9,
+                     "alu": alu_roof(bytes_per_launch / 8.0 / (avg_launch_ms / 1000.0), clocks)},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": statistics.mean(e2e_ms),
                 "h2d_bytes_per_step": int(u0.nbytes), "d2h_bytes_per_step": int(out_host.numel() * 4)},
@@ -382,11 +455,108 @@ def run(args):
         "energy_to_solution": energy,
     }
     ctx.close()
+    del u0_dev
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and args.workload == "fp32_256" and not args.no_c4:
+        line["c4_learned_128"] = c4_learned_128(local)
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+# ------------------------------------------ the learned-propagator comparison
+
+def c4_learned_128(dev_index, steps=3, n_ics=63, epochs=10, batch=8, lr=1e-3):
+    """The learned-coarse-propagator configuration at 128^3, N = 32: the linear
+    learned propagator (stencil skip, nu as a factor), trained here on the
+    pairs the fine solver generates (n_ics seeded k^-2 fields plus white noise,
+    x 32 slices = 2016 pairs), evaluated as one 9^3 kernel per slice, against
+    Parareal with the stencil propagator alone and the serial fine run.  Both
+    Parareal runs use the difference form of the correction.  Times are CUDA
+    events on the contexts' stream; clocks are sampled over the whole
+    comparison, training included."""
+    import torch
+    from paper_1409_8563_gb300 import configs, inputs, native
+    base, u0 = configs.fp32_128()
+    n, N = base.n, base.n_slices
+    nf = round(base.T / N / base.dt_fine)
+    mk = lambda kind, ev: native.Config.make(
+        n, N, base.T, base.dt_fine, base.dt_coarse, base.coarse_factor, fine_dtype=native.F32,
+        coarse_kind=kind, nu0=base.nu0, nu_amp=base.nu_amp, nu_omega=base.nu_omega,
+        learned_skip=native.SKIP_STENCIL, learned_act=native.ACT_LINEAR,
+        correction_form=native.CORRECTION_DIFFERENCE, learned_eval=ev)
+    stream = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            r = None
+            for _ in range(reps):
+                r = fn()
+            e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps, r
+
+    out = {"workload": "learned_128: 128^3, N=32, dt_F=1/2048, stencil G = RK4 on 32^3 at 1/256; "
+                       "linear learned G composed into one 9^3 kernel per slice",
+           "steps": steps}
+    with ClockSampler(dev_index) as clk:
+        trainer = native.Parareal(mk(native.COARSE_LEARNED, native.EVAL_LAYERS), stream=stream)
+        t0 = time.perf_counter()
+        ics = torch.stack([torch.from_numpy(inputs.spectral_ic(n, seed=1000 + i, kmax=32)
+                                            + 0.2 * inputs.random_field(n, seed=2000 + i)).float()
+                           for i in range(n_ics)]).cuda()
+        pu = torch.empty((n_ics * N, n, n, n), dtype=torch.float32, device="cuda")
+        pf = torch.empty_like(pu)
+        torch.cuda.synchronize()          # tensors made on the default stream, used on `stream`
+        sl = trainer.make_pairs(ics, pu, pf)
+        torch.cuda.synchronize()
+        pairs_s = time.perf_counter() - t0
+        del ics
+        trainer.set_coarse_model(inputs.initial_weights(seed=0))
+        t0 = time.perf_counter()
+        hist = trainer.train_coarse(pu, pf, sl, epochs=epochs, batch=batch, lr=lr, seed=1)
+        torch.cuda.synchronize()
+        out["train"] = {"pairs": int(len(sl)), "pairs_s": pairs_s, "epochs": epochs,
+                        "batch": batch, "lr": lr, "train_s": time.perf_counter() - t0,
+                        "loss_first_last": [float(hist[0]), float(hist[-1])]}
+        w = trainer.get_coarse_model()
+        trainer.close()
+        del pu, pf
+        torch.cuda.empty_cache()
+        u = torch.from_numpy(u0).cuda()
+        torch.cuda.synchronize()
+        for name, kind, ev in (("stencil", native.COARSE_STENCIL, native.EVAL_LAYERS),
+                               ("learned", native.COARSE_LEARNED, native.EVAL_COMPOSED)):
+            c = native.Parareal(mk(kind, ev), stream=stream)
+            c.autotune(TUNE_CACHE)
+            if kind == native.COARSE_LEARNED:
+                c.set_coarse_model(w)
+            c.set_problem(u)
+            c.serial_fine(None, as_reference=True)
+            if "serial_fine_ms" not in out:
+                out["serial_fine_ms"], _ = timed(lambda: c.serial_fine(None, as_reference=True), steps)
+
+            def solve(c=c):
+                c.set_problem(u)
+                return c.iterate(N, TOL, native.STOP_DEFECT)
+            solve()
+            ms, (k, h) = timed(solve, steps)
+            src = u.float()
+            dst = torch.empty_like(src)
+            torch.cuda.synchronize()
+            g_ms, _ = timed(lambda: c.propagate(1, src, dst, 1, 1), 10)
+            out[name] = {"k_star": int(k), "time_to_1e-6_ms": ms, "g_apply_ms": g_ms,
+                         "glups_in_solve": sum(N - j for j in range(k)) * n ** 3 * nf / ms / 1e6,
+                         "final_defect": float(h[-1, 2])}
+            c.close()
+    out["learned_over_stencil"] = out["learned"]["time_to_1e-6_ms"] / out["stencil"]["time_to_1e-6_ms"]
+    out["learned_over_serial_fine"] = out["learned"]["time_to_1e-6_ms"] / out["serial_fine_ms"]
+    out["clocks"] = clk.summary()
+    return out
 
 
 # ------------------------------------------------- the other configurations
@@ -767,6 +937,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-c4", action="store_true",
+                    help="skip the 128^3 learned-propagator comparison of the default line")
     ap.add_argument("--workload", default="fp32_256",
                     choices=["fp32_256", "fp32_128", "fp64_32", "learned_128", "learned_512",
                              "learned_g", "batch64", "fine_sweep", "paper_faithful"])
