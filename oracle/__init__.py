@@ -14,6 +14,8 @@ Modules
 ``oracle.modal``    exact discrete solution per Fourier mode (numpy), the
                     analytic solution of Sec. 3 and the speedup model of
                     Sec. 2.2.2.
+``oracle.spectral`` Fourier restriction and prolongation between the fine
+                    and the coarse grid (numpy FFT), Sec. 2.2.2.
 ``oracle.net``      forward / backward of the learned coarse propagator's
                     convolution net, plain FP64, and one Adam step.
 """

@@ -16,7 +16,7 @@ tests follow below.
 """
 import numpy as np
 
-from . import core
+from . import core, spectral
 
 
 def serial_fine(F, u0, n_slices):
@@ -77,6 +77,18 @@ def euler_propagator(problem, dt, steps_per_slice):
     """Forward Euler over one slice (Algorithm 2, with N_c steps per call)."""
     def P(u, n):
         return problem.euler(u, n * steps_per_slice, dt, steps_per_slice)
+    return P
+
+
+def spectral_coarsened_rk4_propagator(problem, r, dt, steps_per_slice, frozen=False):
+    """RK4 on the grid coarsened by r with the spectral transfers (Sec. 2.2.2):
+    Fourier restriction, step, Fourier prolongation."""
+    coarse = problem.with_n(problem.n // r)
+
+    def P(u, n):
+        c = spectral.restrict_spectral(u, r)
+        c = coarse.rk4(c, n * steps_per_slice, dt, steps_per_slice, frozen)
+        return spectral.prolong_spectral(c, r)
     return P
 
 

@@ -354,3 +354,97 @@ def test_difference_form_equals_standard_form_for_a_linear_coarse_propagator():
             assert np.max(np.abs(hs[k][s] - hd[k][s])) < 1e-13 * scale, (k, s)
     fine = opr.serial_fine(F, u0, N)
     assert np.max(np.abs(hd[N][N] - fine[N])) < 1e-13 * scale
+
+
+# ------------------------------------------------ spectral transfers (Sec. 2.2.2)
+
+def _band_limited(n, m, seed, count=6):
+    """Real field of `count` random modes, every component |k_d| <= m/2 - 1."""
+    rng = np.random.default_rng(seed)
+    k = rng.integers(-(m // 2 - 1), m // 2, size=(count, 3)).astype(np.float64)
+    c = rng.standard_normal(count) + 1j * rng.standard_normal(count)
+    return k, c
+
+
+@pytest.mark.parametrize("n,r", [(16, 2), (24, 3), (32, 4), (32, 8)])
+def test_spectral_restriction_samples_band_limited_fields(n, r):
+    """A field made of modes both grids represent is restricted to its exact
+    values at the coarse points (coarse point I on fine point I r)."""
+    from oracle import spectral
+    m = n // r
+    k, c = _band_limited(n, m, seed=n + r)
+    u = modal.field_from_modes(n, k, c)
+    assert np.allclose(spectral.restrict_spectral(u, r), u[::r, ::r, ::r], atol=1e-12, rtol=0)
+
+
+@pytest.mark.parametrize("m,r", [(8, 2), (6, 4), (8, 4)])
+def test_spectral_prolongation_is_the_trigonometric_interpolant(m, r):
+    """P c sampled on the fine grid equals the coarse field's Fourier series
+    evaluated at the fine points, written out mode by mode."""
+    from oracle import spectral
+    k, cf = _band_limited(m * r, m, seed=3 * m + r)
+    c = modal.field_from_modes(m, k, cf)
+    assert np.allclose(spectral.prolong_spectral(c, r), modal.field_from_modes(m * r, k, cf),
+                       atol=1e-12, rtol=0)
+
+
+def test_spectral_transfers_drop_unrepresented_modes_and_keep_the_mean():
+    from oracle import spectral
+    n, r = 16, 4
+    m = n // r
+    for kx in (m // 2, m // 2 + 1, n // 2):            # the coarse Nyquist mode and beyond
+        u = modal.field_from_modes(n, [(kx, 1, 0)], [1.0 + 0.5j])
+        assert np.max(np.abs(spectral.restrict_spectral(u, r))) < 1e-13
+    u = inputs.random_field(n, seed=4) + 3.25
+    assert abs(spectral.restrict_spectral(u, r).mean() - u.mean()) < 1e-13
+    c = inputs.random_field(m, seed=5) - 1.5
+    assert abs(spectral.prolong_spectral(c, r).mean() - c.mean()) < 1e-13
+
+
+def test_spectral_restriction_inverts_prolongation_and_projects():
+    """R P = identity on coarse fields without Nyquist content; P R is a
+    projection (applying it twice changes nothing)."""
+    from oracle import spectral
+    n, r = 24, 3
+    m = n // r
+    k, cf = _band_limited(n, m, seed=11)
+    c = modal.field_from_modes(m, k, cf)
+    assert np.allclose(spectral.restrict_spectral(spectral.prolong_spectral(c, r), r), c,
+                       atol=1e-12, rtol=0)
+    u = inputs.random_field(n, seed=12)
+    pu = spectral.prolong_spectral(spectral.restrict_spectral(u, r), r)
+    assert np.allclose(spectral.prolong_spectral(spectral.restrict_spectral(pu, r), r), pu,
+                       atol=1e-12, rtol=0)
+    assert np.linalg.norm(pu) < np.linalg.norm(u)       # white noise loses its high modes
+
+
+def test_spectral_coarse_parareal_equals_the_modal_recurrence():
+    """With spectral transfers the coarse propagator acts on each fine mode
+    the grids share as the coarse RK4 map at the coarse grid's symbol and
+    removes every other mode, so Parareal (Eq. parareal) decouples into one
+    scalar recurrence per mode.  The field iteration (C stepper on both grids,
+    FFT transfers) must equal that recurrence."""
+    from oracle import parareal as opr
+    from oracle import spectral
+    n, r, N, nf, nc = 16, 2, 3, 6, 2
+    m = n // r
+    a, nu = (1.0, 1.0, 1.0), (0.01, 0.5, 2 * np.pi)
+    dt_f, dt_c = 2.0 ** -9, 3 * 2.0 ** -9
+    P = core.Problem(n, a=a, nu0=nu[0], nu_amp=nu[1], nu_omega=nu[2])
+    F = opr.rk4_propagator(P, dt_f, nf)
+    G = opr.spectral_coarsened_rk4_propagator(P, r, dt_c, nc)
+    u0 = inputs.random_field(n, seed=21)
+    hist = opr.parareal(F, G, u0, N, N)
+
+    k = modal.fft_wavevectors(n).reshape(-1, 3)
+    Lf, Df = modal.symbol_parts(n, a, modal.C2, k)
+    Lc, Dc = modal.symbol_parts(m, a, modal.C2, k)
+    keep = spectral.kept_mask(n, m).ravel()
+    Fm = [modal.rk4_multiplier(Lf, Df, s * nf, dt_f, nf, nu) for s in range(N)]
+    Gm = [np.where(keep, modal.rk4_multiplier(Lc, Dc, s * nc, dt_c, nc, nu), 0.0) for s in range(N)]
+    c0 = np.fft.fftn(u0).ravel()
+    mh = modal.modal_parareal(Fm, Gm, c0, N)
+    for kk in range(N + 1):
+        for s in range(1, N + 1):
+            want = np.real(np.fft.ifftn(mh[kk][s].reshape(n, n, n)))
+            assert np.max(np.abs(hist[kk][s] - want)) < 1e-12 * np.max(np.abs(want)), (kk, s)
