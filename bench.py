@@ -280,6 +280,8 @@ def run(args):
     # (the same iteration, with G's FP32 rounding scaled by the change of its input)
     cfg.correction_form = (native.CORRECTION_DIFFERENCE if args.correction == "difference"
                            else native.CORRECTION_STANDARD)
+    cfg.coarse_transfer = (native.TRANSFER_SPECTRAL if args.transfer == "spectral"
+                           else native.TRANSFER_BOX)
     n, N = cfg.n, cfg.n_slices
     P = n ** 3
     nf = round(cfg.T / N / cfg.dt_fine)
@@ -431,6 +433,7 @@ def run(args):
         "precision": "FP32 stencil; FP64 correction, norms and nu(t)",
         "data": "synthetic",
         "config": {"workload": desc, "correction_form": args.correction,
+                   "coarse_transfer": args.transfer,
                    "n": n, "n_slices": N, "fine_steps_per_slice": nf,
                    "l2": ("inputs larger than L2 (%.2f GB per field set)" % (4.0 * N * P / 1e9)),
                    "parallelism": "replicas" if world > 1 else "single GPU",
@@ -945,6 +948,9 @@ def main():
     ap.add_argument("--slices", type=int, default=8)
     ap.add_argument("--correction", default="difference", choices=["difference", "standard"],
                     help="evaluation of the Parareal correction (fp32_256 / fp32_128 / batch64)")
+    ap.add_argument("--transfer", default="box", choices=["box", "spectral"],
+                    help="fp32_256 / fp32_128: restriction and prolongation of the coarse "
+                         "propagator (box + trilinear, or spectral)")
     ap.add_argument("--tile", default=None,
                     help="fine_sweep: launch shape 'tx,ty,zchunk' (fused kernel, one row per "
                          "thread) or 'path,tx,ty,zchunk' (path 2: two rows per thread) instead of "

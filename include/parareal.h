@@ -119,7 +119,22 @@ typedef struct {
     int learned_act;       /* PARAREAL_ACT_*: the learned propagator's layers */
     int correction_form;   /* PARAREAL_CORRECTION_*: how Eq. (parareal) is evaluated */
     int learned_eval;      /* PARAREAL_EVAL_*: how a LINEAR learned propagator is evaluated */
+    int coarse_transfer;   /* PARAREAL_TRANSFER_*: restriction / prolongation of a coarse-grid G */
 } parareal_config;
+
+/* Transfers between the fine grid and the coarse grid of the stencil coarse
+ * propagator (coarse_factor r > 1; Sec. 2.2.2 notes that a coarse propagator
+ * on a coarser mesh needs them and that their order matters):
+ * BOX      box average over the r^3 fine points of a coarse cell, trilinear
+ *          prolongation from the cell centroids (default);
+ * SPECTRAL the Fourier modes both grids represent (|k_d| <= n/(2r) - 1 on
+ *          every axis) are kept with their coefficients, all others are
+ *          dropped, coarse point I on fine point I r; applied as separable
+ *          real matrices along each axis, in the coarse propagator's
+ *          precision.  Only with coarse_kind STENCIL and r > 1, and with
+ *          n (n / r) elements of G's precision per transfer matrix at most
+ *          160 KiB. */
+enum { PARAREAL_TRANSFER_BOX = 0, PARAREAL_TRANSFER_SPECTRAL = 1 };
 
 /* Layers of the learned coarse propagator (coarse_kind LEARNED / SHIFT):
  * GELU   the network as specified: GELU after the first three convolutions,

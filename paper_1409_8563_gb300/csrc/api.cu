@@ -128,6 +128,16 @@ static parareal_status validate(const parareal_config *cfg, long long *Nf, long 
         *msg = "learned_eval COMPOSED needs learned_act LINEAR (a GELU network is not one convolution)";
         return PARAREAL_E_INVALID;
     }
+    if (cfg->coarse_transfer != PARAREAL_TRANSFER_BOX && cfg->coarse_transfer != PARAREAL_TRANSFER_SPECTRAL) { *msg = "coarse_transfer"; return PARAREAL_E_INVALID; }
+    if (cfg->coarse_transfer == PARAREAL_TRANSFER_SPECTRAL) {
+        if (cfg->coarse_kind != PARAREAL_COARSE_STENCIL || cfg->coarse_factor < 2) {
+            *msg = "spectral transfers need the stencil coarse propagator on a coarsened grid";
+            return PARAREAL_E_INVALID;
+        }
+        const size_t mat = (size_t)cfg->n * (cfg->n / cfg->coarse_factor) *
+                           (cfg->fine_dtype == PARAREAL_F64 ? 8 : 4);
+        if (mat > 160 * 1024) { *msg = "spectral transfer matrices larger than 160 KiB"; return PARAREAL_E_INVALID; }
+    }
     const double slice = cfg->T / cfg->n_slices;
     if (!is_integer_ratio(slice, cfg->dt_fine, Nf)) { *msg = "T/(n_slices dt_fine) must be an integer"; return PARAREAL_E_INVALID; }
     if (!is_integer_ratio(slice, cfg->dt_coarse, Nc)) { *msg = "T/(n_slices dt_coarse) must be an integer"; return PARAREAL_E_INVALID; }
@@ -403,7 +413,13 @@ static parareal_status coarse_apply_t(parareal_ctx *c, const double *Uin, int s,
         return net_apply<T, T>(c, cA, s, static_cast<T *>(out));
     }
     if (c->r > 1) {
-        LK(launch_restrict<T>(Uin, c->n, c->r, cA, c->st));
+        if (c->spectral) {
+            LK(launch_restrict_spectral<T>(Uin, c->n, c->r, static_cast<const T *>(c->sp_R),
+                                           static_cast<const T *>(c->sp_Rt), static_cast<T *>(c->sp_work),
+                                           cA, c->st));
+        } else {
+            LK(launch_restrict<T>(Uin, c->n, c->r, cA, c->st));
+        }
         return rk4_batch<T>(c, c->nc, cA, static_cast<T *>(out), s, 1, c->Nc, c->cfg.dt_coarse,
                             c->coarse_path, c->coarse_tx, c->coarse_ty, c->coarse_zc, cB, cC, cD);
     }
@@ -421,6 +437,25 @@ static parareal_status coarse_apply_t(parareal_ctx *c, const double *Uin, int s,
                         c->coarse_zc, cB, cC, cD);
 }
 
+// The correction with a coarse-grid G: U[p] <- Fv[p] + P(cnew - cold)[p]
+// (trilinear inside the correction kernel, or the spectral prolongation into
+// a fine T field first).  Fv / cold may be null.
+template <typename T>
+static parareal_status correct_coarse(parareal_ctx *c, const T *Fv, const T *cnew, const T *cold,
+                                      double *U, double *dU)
+{
+    if (!c->spectral) {
+        LK((launch_correct<T, T>(Fv, cnew, cold, U, c->n, c->r, c->partials, c->nblk, c->st, dU)));
+        return PARAREAL_OK;
+    }
+    T *fine = static_cast<T *>(c->sp_fine);
+    LK(launch_prolong_spectral<T>(cnew, cold, c->n, c->r, static_cast<const T *>(c->sp_P),
+                                  static_cast<const T *>(c->sp_Pt), static_cast<T *>(c->sp_work), fine,
+                                  c->st));
+    LK((launch_correct<T, T>(Fv, fine, nullptr, U, c->n, 1, c->partials, c->nblk, c->st, dU)));
+    return PARAREAL_OK;
+}
+
 // U[s+1] <- Fv[s+1] + (gnew - gold) with norms into slice_norms[s+1].
 // Fv / gold may be null (read as zero).
 template <typename T>
@@ -430,8 +465,9 @@ static parareal_status correct_t(parareal_ctx *c, int s, const void *gnew, const
     const T *Fv = with_fine ? static_cast<const T *>(c->Fv) + (long long)(s + 1) * c->P : nullptr;
     double *U = c->U + (long long)(s + 1) * c->P;
     if (!c->g_fine) {
-        LK((launch_correct<T, T>(Fv, static_cast<const T *>(gnew), static_cast<const T *>(gold), U,
-                                 c->n, c->r, c->partials, c->nblk, c->st, dU)));
+        parareal_status ps = correct_coarse<T>(c, Fv, static_cast<const T *>(gnew),
+                                               static_cast<const T *>(gold), U, dU);
+        if (ps != PARAREAL_OK) return ps;
     } else {
         LK((launch_correct<T, double>(Fv, static_cast<const double *>(gnew),
                                       static_cast<const double *>(gold), U, c->n, 1, c->partials,
@@ -563,7 +599,8 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, PARAREAL_E_CUDA, "no CUDA device");
         if (std::find(configured.begin(), configured.end(), dev) == configured.end()) {
-            if (configure_rk4_kernels() != cudaSuccess) return fail(nullptr, PARAREAL_E_CUDA, "kernel configuration failed");
+            if (configure_rk4_kernels() != cudaSuccess || configure_spectral_kernels() != cudaSuccess)
+                return fail(nullptr, PARAREAL_E_CUDA, "kernel configuration failed");
             configured.push_back(dev);
         }
     }
@@ -625,6 +662,26 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
     if (cfg->correction_form == PARAREAL_CORRECTION_DIFFERENCE)
         ok = ok && alloc((void **)&c->dA, P * sizeof(double)) && alloc((void **)&c->dB, P * sizeof(double));
     ok = ok && alloc(&c->wS, P * e);
+    c->spectral = cfg->coarse_transfer == PARAREAL_TRANSFER_SPECTRAL;
+    if (c->spectral) {
+        const size_t me = (size_t)c->n * c->nc * e;
+        ok = ok && alloc(&c->sp_R, me) && alloc(&c->sp_Rt, me) && alloc(&c->sp_P, me) &&
+             alloc(&c->sp_Pt, me) && alloc(&c->sp_work, spectral_work_elems(c->n, c->r) * e) &&
+             alloc(&c->sp_fine, P * e);
+        if (ok) {
+            std::vector<double> m4[4];
+            spectral_matrices(c->n, c->r, &m4[0], &m4[1], &m4[2], &m4[3]);
+            void *dst[4] = {c->sp_R, c->sp_Rt, c->sp_P, c->sp_Pt};
+            for (int i = 0; i < 4 && ok; ++i) {
+                if (c->f64) {
+                    ok = cudaMemcpy(dst[i], m4[i].data(), me, cudaMemcpyHostToDevice) == cudaSuccess;
+                } else {
+                    std::vector<float> f(m4[i].begin(), m4[i].end());
+                    ok = cudaMemcpy(dst[i], f.data(), me, cudaMemcpyHostToDevice) == cudaSuccess;
+                }
+            }
+        }
+    }
     c->nblk = correct_blocks(c->P);
     ok = ok && alloc((void **)&c->partials, 5 * sizeof(double) * (size_t)c->nblk);
     ok = ok && alloc((void **)&c->slice_norms, 5 * sizeof(double) * (N + 2));
@@ -655,7 +712,8 @@ extern "C" void parareal_destroy(parareal_ctx *c)
     if (!c) return;
     cudaStreamSynchronize(c->st);
     void *ptrs[] = {c->U, c->Fv, c->gspare, c->wA, c->wB, c->wC, c->cA, c->cB, c->cC, c->cD,
-                    c->tmpd, c->wS, c->ref, c->partials, c->slice_norms, c->dA, c->dB};
+                    c->tmpd, c->wS, c->ref, c->partials, c->slice_norms, c->dA, c->dB,
+                    c->sp_R, c->sp_Rt, c->sp_P, c->sp_Pt, c->sp_work, c->sp_fine};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (void *p : c->gold)
@@ -810,7 +868,7 @@ unsigned long long config_hash(const parareal_config &c)
     for (int d = 0; d < 3; ++d) fnv(h, c.a[d]);
     fnv(h, c.nu0); fnv(h, c.nu_amp); fnv(h, c.nu_omega); fnv(h, c.fine_dtype); fnv(h, c.nu_mode);
     fnv(h, c.coarse_kind); fnv(h, c.learned_skip); fnv(h, c.fine_scheme); fnv(h, c.learned_act);
-    fnv(h, c.correction_form); fnv(h, c.learned_eval);
+    fnv(h, c.correction_form); fnv(h, c.learned_eval); fnv(h, c.coarse_transfer);
     return h;
 }
 }  // namespace
@@ -1120,8 +1178,9 @@ static parareal_status propagate_t(parareal_ctx *c, int which, const void *src, 
             CK(cudaMemsetAsync(res64, 0, P * 8, c->st));
             const T *nullT = nullptr;
             if (!c->g_fine) {
-                LK((launch_correct<T, T>(nullT, static_cast<const T *>(c->gspare), nullptr, res64,
-                                         c->n, c->r, c->partials, c->nblk, c->st)));
+                s = correct_coarse<T>(c, nullT, static_cast<const T *>(c->gspare), nullptr, res64,
+                                      nullptr);
+                if (s != PARAREAL_OK) return s;
             } else {
                 LK((launch_correct<T, double>(nullT, static_cast<const double *>(c->gspare), nullptr,
                                               res64, c->n, 1, c->partials, c->nblk, c->st)));

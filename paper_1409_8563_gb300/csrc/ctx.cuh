@@ -66,6 +66,11 @@ struct parareal_ctx {
     double *dA = nullptr, *dB = nullptr;   // U^{k+1}[n] - U^k[n] (difference-form correction)
     void *wS = nullptr;           // P of T: state of the serial fine run
     double *ref = nullptr;
+    // spectral transfers (coarse_transfer SPECTRAL): matrices R, R^T, P, P^T
+    // in G's precision, three-pass workspace, and the prolonged fine change
+    bool spectral = false;
+    void *sp_R = nullptr, *sp_Rt = nullptr, *sp_P = nullptr, *sp_Pt = nullptr;
+    void *sp_work = nullptr, *sp_fine = nullptr;
     double *partials = nullptr;
     int nblk = 0;
     double *slice_norms = nullptr;  // (N+1) x 5 on device

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 #include "../../include/parareal.h"
 
@@ -118,6 +119,23 @@ cudaError_t launch_convert_f32_to_f64(const float *src, double *dst, long long c
 // Box restriction (factor r) of one FP64 fine field to a T coarse field.
 template <typename T>
 cudaError_t launch_restrict(const double *fine, int n, int r, T *coarse, cudaStream_t st);
+
+// Spectral transfers (spectral.cu): the per-axis matrices in FP64 -- R (m x
+// n), its transpose, P = r R^T (n x m) and its transpose -- and the two
+// transfers, each three passes through `work` (spectral_work_elems(n, r)
+// elements of T).  Restriction reads a fine FP64 field and writes the coarse
+// T field; prolongation writes the fine T field P (cnew - cold) (cold may be
+// null).
+void spectral_matrices(int n, int r, std::vector<double> *R, std::vector<double> *Rt,
+                       std::vector<double> *P, std::vector<double> *Pt);
+size_t spectral_work_elems(int n, int r);
+cudaError_t configure_spectral_kernels();
+template <typename T>
+cudaError_t launch_restrict_spectral(const double *fine, int n, int r, const T *R, const T *Rt,
+                                     T *work, T *coarse, cudaStream_t st);
+template <typename T>
+cudaError_t launch_prolong_spectral(const T *cnew, const T *cold, int n, int r, const T *P,
+                                    const T *Pt, T *work, T *fine, cudaStream_t st);
 
 // Correction of Eq. (parareal) for one slice, with per-block norm partials:
 //   U[p] <- Fv[p] + (g_new[p] - g_old[p]),  g = trilinear prolongation of the
