@@ -213,6 +213,29 @@ parareal_status parareal_coarse_sweep(parareal_ctx *ctx, int first_slice, int co
 parareal_status parareal_iterate(parareal_ctx *ctx, int k_max, double tol, int stop_rule,
                                  int *k_done, double *hist);
 
+/* The iterations of parareal_iterate, with the same arguments, results and
+ * iterates (bit for bit), run as ONE CUDA graph launch with the stopping
+ * test on the device instead of one host round trip per iteration.  The
+ * graph (conditional nodes) is a WHILE loop whose pass selects, with a
+ * SWITCH on the number K of slices already exact, the iteration body
+ * captured for that K (Eq. parareal for slices K..N_p-1: batched fine
+ * sweep, serial coarse sweep with corrections, norms), followed by a
+ * one-thread kernel that applies the stopping rule to the norms and ends
+ * the loop (Sec. 2.2.4 criteria).  No counterpart in the paper: its loop
+ * runs on the host of each node.
+ * - The first call captures N_p bodies and instantiates the graph (once per
+ *   context); it is rebuilt when the launch shapes change (parareal_autotune)
+ *   or a reference is set or cleared.  Weights of a learned propagator may
+ *   change between calls.
+ * - hist[4 i + 3] is device time (ms, %globaltimer) since the first
+ *   iteration of the call started.
+ * - The context must have been advanced only by parareal_iterate and this
+ *   call since parareal_set_problem (else PARAREAL_E_STATE); kernel timing
+ *   (parareal_profile) does not see the launches inside the graph.
+ * - Synchronises the context stream.  Errors as parareal_iterate. */
+parareal_status parareal_iterate_device(parareal_ctx *ctx, int k_max, double tol, int stop_rule,
+                                        int *k_done, double *hist);
+
 /* Per-slice residuals of the current iterate; per_slice_out receives
  * n_slices + 1 doubles (index 0 = u0, always 0). */
 parareal_status parareal_residual(parareal_ctx *ctx, int kind, double *per_slice_out);

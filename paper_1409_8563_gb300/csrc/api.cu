@@ -483,13 +483,14 @@ static parareal_status correct_t(parareal_ctx *c, int s, const void *gnew, const
 static parareal_status coarse_chain(parareal_ctx *c, int first, int count, bool chain)
 {
     for (int s = first; s < first + count; ++s) {
-        parareal_status ps = DISPATCH(c, coarse_apply_t, c->U + (long long)s * c->P, s, c->gspare);
+        void *g = g_next(c, s + 1);
+        parareal_status ps = DISPATCH(c, coarse_apply_t, c->U + (long long)s * c->P, s, g);
         if (ps != PARAREAL_OK) return ps;
         if (chain) {
-            ps = DISPATCH(c, correct_t, s, c->gspare, nullptr, false);
+            ps = DISPATCH(c, correct_t, s, g, nullptr, false);
             if (ps != PARAREAL_OK) return ps;
         }
-        std::swap(c->gspare, c->gold[s + 1]);
+        c->gcur[s + 1] ^= 1;
     }
     return PARAREAL_OK;
 }
@@ -499,7 +500,7 @@ static parareal_status coarse_chain(parareal_ctx *c, int first, int count, bool 
 // fine sweep of slices K..N-1, then the serial coarse sweep with the
 // correction and per-slice norms, then (with a reference) the defect norms
 // into slot N+1 of slice_norms.  K = c->k_total: U[0..K] are already exact.
-parareal_status iter_enqueue(parareal_ctx *c)
+parareal_status iter_enqueue(parareal_ctx *c, bool copy_norms)
 {
     const int K = c->k_total;
     parareal_status s = DISPATCH(c, fine_sweep_t, K, c->N - K);
@@ -508,7 +509,7 @@ parareal_status iter_enqueue(parareal_ctx *c)
         // U[n+1] = Fv[n+1] + G(D_n), D_n = U^{k+1}[n] - U^k[n] (G linear); the
         // correction of slice n writes D_{n+1}.  D_K = 0: slice K+1 takes Fv alone.
         double *Din = c->dA, *Dout = c->dB;
-        s = DISPATCH(c, correct_t, K, c->gold[K + 1], c->gold[K + 1], true, Din);
+        s = DISPATCH(c, correct_t, K, g_cur(c, K + 1), g_cur(c, K + 1), true, Din);
         if (s != PARAREAL_OK) return s;
         for (int n = K + 1; n < c->N; ++n) {
             s = DISPATCH(c, coarse_apply_t, Din, n, c->gspare);
@@ -519,22 +520,24 @@ parareal_status iter_enqueue(parareal_ctx *c)
         }
     } else {
         // slice K+1: its input U[K] did not change, so G's difference is zero
-        s = DISPATCH(c, correct_t, K, c->gold[K + 1], c->gold[K + 1], true);
+        s = DISPATCH(c, correct_t, K, g_cur(c, K + 1), g_cur(c, K + 1), true);
         if (s != PARAREAL_OK) return s;
         for (int n = K + 1; n < c->N; ++n) {
-            s = DISPATCH(c, coarse_apply_t, c->U + (long long)n * c->P, n, c->gspare);
+            void *g = g_next(c, n + 1);
+            s = DISPATCH(c, coarse_apply_t, c->U + (long long)n * c->P, n, g);
             if (s != PARAREAL_OK) return s;
-            s = DISPATCH(c, correct_t, n, c->gspare, c->gold[n + 1], true);
+            s = DISPATCH(c, correct_t, n, g, g_cur(c, n + 1), true);
             if (s != PARAREAL_OK) return s;
-            std::swap(c->gspare, c->gold[n + 1]);
+            c->gcur[n + 1] ^= 1;
         }
     }
     if (c->has_ref) {
         LK(launch_diff_norms<double>(c->U + (long long)c->N * c->P, c->ref, c->P, c->partials, c->nblk, c->st));
         LK(launch_reduce_partials(c->partials, c->nblk, c->slice_norms + 5ll * (c->N + 1), c->st));
     }
-    CK(cudaMemcpyAsync(c->h_norms, c->slice_norms, sizeof(double) * 5 * (c->N + 2),
-                       cudaMemcpyDeviceToHost, c->st));
+    if (copy_norms)
+        CK(cudaMemcpyAsync(c->h_norms, c->slice_norms, sizeof(double) * 5 * (c->N + 2),
+                           cudaMemcpyDeviceToHost, c->st));
     return PARAREAL_OK;
 }
 
@@ -653,7 +656,9 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
     ok = ok && alloc((void **)&c->U, (N + 1) * P * sizeof(double));
     ok = ok && alloc(&c->Fv, (N + 1) * P * e);
     c->gold.assign(N + 1, nullptr);
-    for (size_t i = 1; ok && i <= N; ++i) ok = alloc(&c->gold[i], gbytes);
+    c->gold2.assign(N + 1, nullptr);
+    c->gcur.assign(N + 1, 0);
+    for (size_t i = 1; ok && i <= N; ++i) ok = alloc(&c->gold[i], gbytes) && alloc(&c->gold2[i], gbytes);
     ok = ok && alloc(&c->gspare, gbytes);
     ok = ok && alloc(&c->wA, N * P * e) && alloc(&c->wB, N * P * e) && alloc(&c->wC, N * P * e);
     const size_t cbytes = (c->r > 1 ? Pc : P) * e;
@@ -718,8 +723,11 @@ extern "C" void parareal_destroy(parareal_ctx *c)
         if (p) cudaFree(p);
     for (void *p : c->gold)
         if (p) cudaFree(p);
+    for (void *p : c->gold2)
+        if (p) cudaFree(p);
     if (c->h_norms) cudaFreeHost(c->h_norms);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    solve_graph_free(c);
     net_free(c);
     delete c;
 }
@@ -935,7 +943,7 @@ extern "C" parareal_status parareal_save_state(parareal_ctx *c, void *host, size
     CK(cudaMemcpyAsync(p, c->U, ub, cudaMemcpyDeviceToHost, c->st));
     p += ub;
     for (int i = 1; i <= c->N; ++i, p += gold_bytes(c))
-        CK(cudaMemcpyAsync(p, c->gold[i], gold_bytes(c), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(p, g_cur(c, i), gold_bytes(c), cudaMemcpyDeviceToHost, c->st));
     if (c->has_ref) CK(cudaMemcpyAsync(p, c->ref, (size_t)c->P * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     return PARAREAL_OK;
@@ -969,7 +977,7 @@ extern "C" parareal_status parareal_load_state(parareal_ctx *c, const void *host
     CK(cudaMemcpyAsync(c->U, p, ub, cudaMemcpyHostToDevice, c->st));
     p += ub;
     for (int i = 1; i <= c->N; ++i, p += gold_bytes(c))
-        CK(cudaMemcpyAsync(c->gold[i], p, gold_bytes(c), cudaMemcpyHostToDevice, c->st));
+        CK(cudaMemcpyAsync(g_cur(c, i), p, gold_bytes(c), cudaMemcpyHostToDevice, c->st));
     if (c->has_ref) CK(cudaMemcpyAsync(c->ref, p, (size_t)c->P * sizeof(double), cudaMemcpyHostToDevice, c->st));
     CK(cudaStreamSynchronize(c->st));
     c->k_total = h.k_total;
@@ -1006,6 +1014,7 @@ extern "C" parareal_status parareal_iterate(parareal_ctx *c, int k_max, double t
     if (stop_rule < 0 || stop_rule > 2) return fail(c, PARAREAL_E_INVALID, "stop_rule");
     parareal_status s;
     if (!c->started) {
+        std::fill(c->gcur.begin(), c->gcur.end(), 0);
         s = coarse_chain(c, 0, c->N, true);
         if (s != PARAREAL_OK) return s;
         c->started = true;

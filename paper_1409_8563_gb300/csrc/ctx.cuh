@@ -46,6 +46,8 @@ struct NetState {
     bool has_model = false;
 };
 
+struct SolveGraph;                // solve_graph.cu: the captured iteration loop
+
 struct parareal_ctx {
     parareal_config cfg{};
     cudaStream_t st = nullptr;
@@ -58,8 +60,13 @@ struct parareal_ctx {
 
     double *U = nullptr;
     void *Fv = nullptr;
-    std::vector<void *> gold;     // gold[s] = G(U^k[s-1]) for s = 1..N (index 0 unused)
-    void *gspare = nullptr;
+    // G(U^k[s-1]) for s = 1..N (index 0 unused) lives in gold[s] or gold2[s]:
+    // gcur[s] names the current one, the other receives the next G output.
+    // The roles follow from the iteration count alone (no pointer swaps), so
+    // work enqueued for a given iteration is the same whenever it is built.
+    std::vector<void *> gold, gold2;
+    std::vector<int> gcur;
+    void *gspare = nullptr;       // scratch G output (difference form, propagate)
     void *wA = nullptr, *wB = nullptr, *wC = nullptr;
     void *cA = nullptr, *cB = nullptr, *cC = nullptr, *cD = nullptr;
     double *tmpd = nullptr;       // 2P doubles: conversions and propagate() scratch
@@ -88,6 +95,7 @@ struct parareal_ctx {
     int coarse_path = PATH_FUSED, coarse_tx = 32, coarse_ty = 8, coarse_zc = 0;
 
     NetState net;
+    SolveGraph *sgraph = nullptr;
 
     std::string err;
     long long launches = 0;
@@ -101,6 +109,10 @@ struct parareal_ctx {
 };
 
 parareal_status fail(parareal_ctx *c, parareal_status s, const std::string &msg);
+
+// The current and the next buffer of the stored G output of slice s.
+inline void *g_cur(parareal_ctx *c, int s) { return c->gcur[s] ? c->gold2[s] : c->gold[s]; }
+inline void *g_next(parareal_ctx *c, int s) { return c->gcur[s] ? c->gold[s] : c->gold2[s]; }
 
 #define CK(call)                                                                              \
     do {                                                                                      \
@@ -127,12 +139,15 @@ parareal_status euler_batch(parareal_ctx *c, int m, const T *in, T *out, int fir
                             int count, long long nsteps, double dt, int op, T *ws1, T *ws2);
 
 // api.cu: one Parareal iteration split into device work and host bookkeeping
-parareal_status iter_enqueue(parareal_ctx *c);
+parareal_status iter_enqueue(parareal_ctx *c, bool copy_norms = true);
 parareal_status iter_finish(parareal_ctx *c, double *dmax, double *l2max, double *d);
 
 // api.cu: the stencil coarse propagator of slice s, prolonged to the fine
 // grid in FP64 (the skip path of the stencil-corrected learned propagator)
 parareal_status stencil_g_fine(parareal_ctx *c, const double *u, int s, double *out);
+
+// solve_graph.cu
+void solve_graph_free(parareal_ctx *c);
 
 // learned.cu
 parareal_status net_check(parareal_ctx *c);

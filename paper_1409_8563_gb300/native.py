@@ -87,6 +87,7 @@ SIGNATURES = {
     "parareal_fine_sweep": (_i, [_vp, _i, _i]),
     "parareal_coarse_sweep": (_i, [_vp, _i, _i, _i]),
     "parareal_iterate": (_i, [_vp, _i, _d, _i, _ip, _dp]),
+    "parareal_iterate_device": (_i, [_vp, _i, _d, _i, _ip, _dp]),
     "parareal_residual": (_i, [_vp, _i, _dp]),
     "parareal_set_reference": (_i, [_vp, _vp, _i, _i]),
     "parareal_serial_fine": (_i, [_vp, _vp, _i, _i, _i]),
@@ -205,10 +206,13 @@ class Parareal:
     def coarse_sweep(self, first, count, chain=1):
         return self._check(lib().parareal_coarse_sweep(self._h, first, count, chain))
 
-    def iterate(self, k_max, tol=0.0, stop_rule=STOP_NONE):
+    def iterate(self, k_max, tol=0.0, stop_rule=STOP_NONE, device=False):
+        """Run up to k_max iterations; device=True runs them as one CUDA graph
+        launch with the stopping test on the device (parareal_iterate_device)."""
         k = ctypes.c_int()
         hist = (ctypes.c_double * (4 * max(k_max, 1)))()
-        self._check(lib().parareal_iterate(self._h, k_max, tol, stop_rule, ctypes.byref(k), hist))
+        fn = lib().parareal_iterate_device if device else lib().parareal_iterate
+        self._check(fn(self._h, k_max, tol, stop_rule, ctypes.byref(k), hist))
         h = np.array(hist[:4 * k.value]).reshape(k.value, 4)
         return k.value, h
 
