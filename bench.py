@@ -372,6 +372,18 @@ def run(args):
     updates = sum_over_ranks(dist, updates)
     value = updates / (total_ms / 1000.0) / 1e9
 
+    # the same solve as one CUDA graph launch with the stopping test on the
+    # device (parareal_iterate_device): one warm-up (builds the graph), one timed
+    ctx.set_problem(u0_dev)
+    ctx.iterate(N, TOL, native.STOP_DEFECT, device=True)
+    with torch.cuda.stream(stream):
+        ctx.set_problem(u0_dev)
+        ev0.record(stream)
+        k_dev, h_dev = ctx.iterate(N, TOL, native.STOP_DEFECT, device=True)
+        ev1.record(stream)
+    ev1.synchronize()
+    device_loop_ms = ev0.elapsed_time(ev1)
+
     # end to end through the C ABI with host buffers: H2D of u0 and D2H of
     # the final slice inside every timed step
     e2e_ms = []
@@ -440,6 +452,7 @@ def run(args):
                    "launch_shapes": {"fine_sweep": list(fine_shape), "coarse": list(coarse_shape),
                                      "serial_fine": list(serial_shape)}},
         "time_to_1e-6_ms": total_ms / args.steps,
+        "time_to_1e-6_device_loop_ms": device_loop_ms, "k_star_device_loop": k_dev,
         "serial_fine_ms": serial_ms,
         "parareal_over_serial": (total_ms / args.steps) / serial_ms,
         "k_star": k_star, "final_defect": final_defect,
@@ -477,8 +490,9 @@ def c4_learned_128(dev_index, steps=3, n_ics=63, epochs=10, batch=8, lr=1e-3):
     pairs the fine solver generates (n_ics seeded k^-2 fields plus white noise,
     x 32 slices = 2016 pairs), evaluated as one 9^3 kernel per slice, against
     Parareal with the stencil propagator alone and the serial fine run.  Both
-    Parareal runs use the difference form of the correction.  Times are CUDA
-    events on the contexts' stream; clocks are sampled over the whole
+    Parareal runs use the difference form of the correction and run as one
+    graph launch each (parareal_iterate_device).  Times are CUDA events on
+    the contexts' stream; clocks are sampled over the whole
     comparison, training included."""
     import torch
     from paper_1409_8563_gb300 import configs, inputs, native
@@ -545,7 +559,7 @@ def c4_learned_128(dev_index, steps=3, n_ics=63, epochs=10, batch=8, lr=1e-3):
 
             def solve(c=c):
                 c.set_problem(u)
-                return c.iterate(N, TOL, native.STOP_DEFECT)
+                return c.iterate(N, TOL, native.STOP_DEFECT, device=True)
             solve()
             ms, (k, h) = timed(solve, steps)
             src = u.float()
@@ -588,15 +602,18 @@ def run_fp64_32(args):
     ctx.serial_fine(None, as_reference=True)
     serial_ms, _ = _timed(lambda: ctx.serial_fine(None, as_reference=True), 3)
 
-    def solve():
+    def solve(device=False):
         ctx.set_problem(u)
-        return ctx.iterate(cfg.n_slices, TOL, native.STOP_DEFECT)
+        return ctx.iterate(cfg.n_slices, TOL, native.STOP_DEFECT, device=device)
     for _ in range(args.warmup):
         solve()
+        solve(True)
     ms, (k, h) = _timed(solve, args.steps)
+    ms_dev, _ = _timed(lambda: solve(True), args.steps)
     P, N, nf = 32 ** 3, cfg.n_slices, round(cfg.T / cfg.n_slices / cfg.dt_fine)
     ups = sum(N - j for j in range(k)) * P * nf
     print(json.dumps({"workload": "fp64_32", "time_to_1e-6_ms": ms, "serial_fine_ms": serial_ms,
+                      "time_to_1e-6_device_loop_ms": ms_dev,
                       "parareal_over_serial": ms / serial_ms, "k_star": k,
                       "defects": [float(x) for x in h[:, 2]], "glups_in_solve": ups / ms / 1e6,
                       "dtype": "f64", "steps": args.steps, "warmup": args.warmup}))
