@@ -430,6 +430,19 @@ parareal_status parareal_load_state(parareal_ctx *ctx, const void *host, size_t 
  * stays usable afterwards.  No counterpart in the paper. */
 parareal_status parareal_selftest_timeout(void *cuda_stream);
 
+/* Failure-detection self-test of the grid barrier of the persistent RK4
+ * path (launch path 3: all steps of a sweep in one cooperative launch, the
+ * blocks meeting at a grid barrier between stages).  One cooperative launch
+ * of one block per SM in which block 0 leaves without arriving: every other
+ * block's bounded wait (about 2^20 polls) gives up and sets the error flag,
+ * which the host reads.  Returns PARAREAL_E_TIMEOUT when the waits gave up
+ * as designed, PARAREAL_OK if they did not (a broken wait), PARAREAL_E_CUDA
+ * on a CUDA error.  Allocates 16 bytes of device memory; the device stays
+ * usable.  A context whose persistent launch gives up the same way reports
+ * PARAREAL_E_TIMEOUT from the call that ran it and stays usable.  No
+ * counterpart in the paper. */
+parareal_status parareal_selftest_grid_barrier(void *cuda_stream);
+
 /* Number of kernel launches this context issued so far (for reporting). */
 long long parareal_launch_count(const parareal_ctx *ctx);
 

@@ -173,7 +173,12 @@ extern "C" parareal_status parareal_stability(const parareal_config *cfg, double
 // cheap), staged path for FP64 (FP64 throughput-bound; no recompute).
 static void default_tiles(int dtype, int n, int count, int *path, int *tx, int *ty, int *zc)
 {
-    *path = dtype == PARAREAL_F64 ? PATH_STAGED : PATH_FUSED;
+    // FP64: no halo recomputation (the FP64 rate bounds the step); a small
+    // batch is a few microseconds of work per stage, so one persistent launch
+    // per sweep replaces four launches per step
+    *path = dtype == PARAREAL_F64
+                ? ((long long)count * n * n * n <= (1ll << 22) ? PATH_PERSIST : PATH_STAGED)
+                : PATH_FUSED;
     const int cand[][2] = {{64, 16}, {32, 16}, {32, 8}, {16, 16}};
     const int candd[][2] = {{32, 8}, {16, 16}, {16, 8}};
     *tx = *ty = 0;
@@ -184,7 +189,7 @@ static void default_tiles(int dtype, int n, int count, int *path, int *tx, int *
         for (auto &t : candd)
             if (rk4_fused_supported(dtype, n, t[0], t[1], 1)) { *tx = t[0]; *ty = t[1]; break; }
     }
-    if (*tx == 0) { *path = PATH_STAGED; *tx = 16; *ty = 8; }
+    if (*tx == 0) { *path = *path == PATH_PERSIST ? PATH_PERSIST : PATH_STAGED; *tx = 16; *ty = 8; }
     // z chunk: whole columns unless the launch would leave SMs idle
     int z = n;
     while (z > 16 && (long long)count * (n / *tx) * (n / *ty) * ((n + z - 1) / z) < 2ll * sm_count()) z /= 2;
@@ -197,7 +202,7 @@ static bool tile_override(const char *var, int dtype, int n, int *path, int *tx,
     if (!e || !*e) return true;
     int p, x, y, z;
     if (std::sscanf(e, "%d,%d,%d,%d", &p, &x, &y, &z) != 4) return false;
-    if (!is_fused(p) && p != PATH_STAGED) return false;
+    if (!is_fused(p) && p != PATH_STAGED && p != PATH_PERSIST) return false;
     if (is_fused(p) && (!rk4_fused_supported(dtype, n, x, y, fused_rows(p)) || z < 1)) return false;
     *path = p; *tx = x; *ty = y; *zc = z;
     return true;
@@ -255,6 +260,11 @@ parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, int first
             }
             src = dst;
         }
+    } else if (path == PATH_PERSIST) {
+        if (in != out)
+            CK(cudaMemcpyAsync(out, in, (size_t)count * a.P * sizeof(T), cudaMemcpyDeviceToDevice, c->st));
+        LK(launch_rk4_persist<T>(a, out, ws1, ws2, ws3, nsteps, c->bar, c->st));
+        c->persist_used = true;
     } else {
         if (in != out)
             CK(cudaMemcpyAsync(out, in, (size_t)count * a.P * sizeof(T), cudaMemcpyDeviceToDevice, c->st));
@@ -637,8 +647,9 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
     }
     c->fine_op = cfg->fine_scheme == PARAREAL_SCHEME_C4 ? OP_C4 : OP_C2;
     if (c->fine_op != OP_C2) {
-        // the fused kernel implements the 7-point operator only
-        c->fine_path = c->ser_path = PATH_STAGED;
+        // the fused kernels implement the 7-point operator only
+        if (is_fused(c->fine_path)) c->fine_path = PATH_STAGED;
+        if (is_fused(c->ser_path)) c->ser_path = PATH_STAGED;
     }
 
     auto alloc = [&](void **p, size_t bytes) -> bool {
@@ -667,6 +678,8 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
     if (cfg->correction_form == PARAREAL_CORRECTION_DIFFERENCE)
         ok = ok && alloc((void **)&c->dA, P * sizeof(double)) && alloc((void **)&c->dB, P * sizeof(double));
     ok = ok && alloc(&c->wS, P * e);
+    ok = ok && alloc((void **)&c->bar, sizeof(pr::GridBarrier)) &&
+         cudaMemset(c->bar, 0, sizeof(pr::GridBarrier)) == cudaSuccess;
     c->spectral = cfg->coarse_transfer == PARAREAL_TRANSFER_SPECTRAL;
     if (c->spectral) {
         const size_t me = (size_t)c->n * c->nc * e;
@@ -718,7 +731,7 @@ extern "C" void parareal_destroy(parareal_ctx *c)
     cudaStreamSynchronize(c->st);
     void *ptrs[] = {c->U, c->Fv, c->gspare, c->wA, c->wB, c->wC, c->cA, c->cB, c->cC, c->cD,
                     c->tmpd, c->wS, c->ref, c->partials, c->slice_norms, c->dA, c->dB,
-                    c->sp_R, c->sp_Rt, c->sp_P, c->sp_Pt, c->sp_work, c->sp_fine};
+                    c->sp_R, c->sp_Rt, c->sp_P, c->sp_Pt, c->sp_work, c->sp_fine, c->bar};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (void *p : c->gold)
@@ -844,6 +857,41 @@ extern "C" parareal_status parareal_set_slice(parareal_ctx *c, int slice, const 
     if (!c) return PARAREAL_E_INVALID;
     if (slice < 0 || slice > c->N) return fail(c, PARAREAL_E_INVALID, "slice out of range");
     return load_field(c, c->U + (long long)slice * c->P, src, dtype, mem);
+}
+
+extern "C" parareal_status parareal_selftest_grid_barrier(void *cuda_stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    pr::GridBarrier *b = nullptr;
+    if (cudaMalloc((void **)&b, sizeof *b) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, PARAREAL_E_NOMEM, "self-test barrier allocation failed");
+    }
+    pr::GridBarrier h{};
+    cudaError_t e = cudaMemsetAsync(b, 0, sizeof *b, st);
+    if (e == cudaSuccess) e = launch_grid_barrier_selftest(b, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, b, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(b);
+    if (e != cudaSuccess) return fail(nullptr, PARAREAL_E_CUDA, std::string("self-test: ") + cudaGetErrorString(e));
+    if (h.err == 1) return fail(nullptr, PARAREAL_E_TIMEOUT, "grid barrier gave up as designed (self-test)");
+    return PARAREAL_OK;
+}
+
+parareal_status device_check(parareal_ctx *c)
+{
+    if (c->persist_used) {
+        pr::GridBarrier h{};
+        CK(cudaMemcpyAsync(&h, c->bar, sizeof h, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        c->persist_used = false;
+        if (h.err) {
+            // blocks may have left a barrier half counted: start the next launch clean
+            CK(cudaMemsetAsync(c->bar, 0, sizeof h, c->st));
+            return fail(c, PARAREAL_E_TIMEOUT, "a grid barrier of the persistent RK4 kernel gave up waiting");
+        }
+    }
+    return net_check(c);
 }
 
 // ----------------------------------------------------------- checkpoint
@@ -1025,7 +1073,7 @@ extern "C" parareal_status parareal_iterate(parareal_ctx *c, int k_max, double t
         s = iter_enqueue(c);
         if (s != PARAREAL_OK) return s;
         CK(cudaStreamSynchronize(c->st));
-        s = net_check(c);
+        s = device_check(c);
         if (s != PARAREAL_OK) return s;
         double dmax, l2max, d;
         s = iter_finish(c, &dmax, &l2max, &d);
@@ -1143,7 +1191,7 @@ extern "C" parareal_status parareal_serial_fine(parareal_ctx *c, void *dst, int 
             CK(cudaStreamSynchronize(c->st));
         }
     }
-    return PARAREAL_OK;
+    return c->persist_used ? device_check(c) : PARAREAL_OK;
 }
 
 template <typename T>
@@ -1213,7 +1261,7 @@ extern "C" parareal_status parareal_propagate(parareal_ctx *c, int which, const 
     if (dtype != PARAREAL_F32 && dtype != PARAREAL_F64) return fail(c, PARAREAL_E_INVALID, "dtype");
     if (first < 0 || count < 0 || first + count > c->N) return fail(c, PARAREAL_E_INVALID, "slice range");
     parareal_status s = DISPATCH(c, propagate_t, which, src, dst, dtype, first, count);
-    return s != PARAREAL_OK ? s : net_check(c);
+    return s != PARAREAL_OK ? s : device_check(c);
 }
 
 // ----------------------------------------------------------------- autotune
@@ -1262,6 +1310,7 @@ static void candidates(int dtype, int m, std::vector<std::array<int, 4>> *out)
             }
         }
     out->push_back({PATH_STAGED, 16, 8, m});
+    out->push_back({PATH_PERSIST, 16, 8, m});
 }
 
 static std::string tune_key(int dtype, int m, int count)
@@ -1311,7 +1360,8 @@ static parareal_status tune_one(parareal_ctx *c, const char *cache, int m, int c
     const std::string key = tune_key(dtype, m, count);
     int sh[4];
     if (cache_lookup(cache, key, sh) &&
-        (sh[0] == PATH_STAGED || (is_fused(sh[0]) && rk4_fused_supported(dtype, m, sh[1], sh[2], fused_rows(sh[0]))))) {
+        (sh[0] == PATH_STAGED || sh[0] == PATH_PERSIST ||
+         (is_fused(sh[0]) && rk4_fused_supported(dtype, m, sh[1], sh[2], fused_rows(sh[0]))))) {
         *path = sh[0]; *tx = sh[1]; *ty = sh[2]; *zc = sh[3];
         *best_ms = -1.0;
         return PARAREAL_OK;

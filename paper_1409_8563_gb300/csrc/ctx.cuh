@@ -10,8 +10,10 @@
 #include "internal.cuh"
 
 // Launch paths of an RK4 sweep: the fused kernel with one region row per
-// thread, the per-stage kernels, the fused kernel with two rows per thread.
-enum { PATH_FUSED = 0, PATH_STAGED = 1, PATH_FUSED2 = 2 };
+// thread, the per-stage kernels, the fused kernel with two rows per thread,
+// and the per-stage arithmetic as one persistent cooperative launch per
+// sweep (grid barriers between stages; small grids).
+enum { PATH_FUSED = 0, PATH_STAGED = 1, PATH_FUSED2 = 2, PATH_PERSIST = 3 };
 // region rows per thread of a fused launch path
 inline int fused_rows(int path) { return path == PATH_FUSED2 ? 2 : 1; }
 inline bool is_fused(int path) { return path == PATH_FUSED || path == PATH_FUSED2; }
@@ -73,6 +75,8 @@ struct parareal_ctx {
     double *dA = nullptr, *dB = nullptr;   // U^{k+1}[n] - U^k[n] (difference-form correction)
     void *wS = nullptr;           // P of T: state of the serial fine run
     double *ref = nullptr;
+    pr::GridBarrier *bar = nullptr;   // barrier state of the persistent RK4 kernel
+    bool persist_used = false;        // a persistent launch ran since the last check
     // spectral transfers (coarse_transfer SPECTRAL): matrices R, R^T, P, P^T
     // in G's precision, three-pass workspace, and the prolonged fine change
     bool spectral = false;
@@ -148,6 +152,10 @@ parareal_status stencil_g_fine(parareal_ctx *c, const double *u, int s, double *
 
 // solve_graph.cu
 void solve_graph_free(parareal_ctx *c);
+
+// api.cu: status of the device-side waits since the last check (persistent
+// RK4 grid barriers, tensor-core completion waits); synchronises the stream
+parareal_status device_check(parareal_ctx *c);
 
 // learned.cu
 parareal_status net_check(parareal_ctx *c);

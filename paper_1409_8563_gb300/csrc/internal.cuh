@@ -110,6 +110,26 @@ template <typename T>
 cudaError_t launch_rk4_stage(const StepArgs &a, int stage, const T *ysrc, T *u, T *ydst,
                              T *acc, cudaStream_t st);
 
+// Grid-wide barrier state of the persistent RK4 kernel (device memory,
+// zero-initialised; err becomes 1 when a barrier wait gave up).
+struct GridBarrier {
+    unsigned count, gen;
+    int err, pad;
+};
+constexpr int PERSIST_MAX_FIELDS = 64;
+
+// All nsteps RK4 steps of `count` fields in one cooperative launch (per 64
+// fields), the per-stage arithmetic of launch_rk4_stage with a grid barrier
+// between stages: u is advanced in place; y1, y2, acc are workspaces of the
+// same size.  a.j is ignored (steps 0..nsteps-1 of the slice).
+template <typename T>
+cudaError_t launch_rk4_persist(const StepArgs &a, T *u, T *y1, T *y2, T *acc, long long nsteps,
+                               GridBarrier *bar, cudaStream_t st);
+
+// Self-test: a cooperative launch in which one block never reaches the grid
+// barrier (every other block's bounded wait gives up and sets b->err).
+cudaError_t launch_grid_barrier_selftest(GridBarrier *b, cudaStream_t st);
+
 // Elementwise conversions / copies of a batch of fields.
 cudaError_t launch_convert_f64_to_f32(const double *src, float *dst, long long count,
                                       cudaStream_t st);

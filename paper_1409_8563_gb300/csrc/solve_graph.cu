@@ -282,7 +282,8 @@ extern "C" parareal_status parareal_iterate_device(parareal_ctx *c, int k_max, d
     CK(cudaMemcpyAsync(c->h_norms, c->slice_norms, sizeof(double) * 5 * (c->N + 2),
                        cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
-    s = net_check(c);
+    c->persist_used = true;      // the bodies may hold persistent launches
+    s = device_check(c);
     if (s != PARAREAL_OK) return s;
     const int K0 = c->k_total;
     for (int i = 0; i < h.done; ++i) c->launches += g->body_launches[K0 + i];

@@ -650,6 +650,201 @@ template cudaError_t launch_rk4_stage<float>(const StepArgs &, int, const float 
 template cudaError_t launch_rk4_stage<double>(const StepArgs &, int, const double *, double *,
                                               double *, double *, cudaStream_t);
 
+// ------------------------------------------------------ persistent RK4
+
+// Grid-wide barrier of a cooperative launch.  The last block to arrive
+// resets the count and advances the generation; the others wait for the
+// generation to change, for at most BARRIER_LIMIT polls, after which they
+// set the error flag and every block leaves at its next barrier.
+constexpr long long BARRIER_LIMIT = 1ll << 20;
+
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void atom_add_release(unsigned *p, unsigned v)
+{
+    asm volatile("red.add.release.gpu.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// The block's writes before the barrier reach the other blocks through the
+// CTA barrier followed by thread 0's acquire-release arrival; the waiting
+// blocks acquire the new generation.
+__device__ __forceinline__ bool grid_sync_bounded(GridBarrier *b, unsigned nblocks, unsigned &gen)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = gen;
+        if (atom_add_acq_rel(&b->count, 1u) == nblocks - 1) {
+            atomicExch(&b->count, 0u);
+            atom_add_release(&b->gen, 1u);
+        } else {
+            long long i = 0;
+            while (ld_acquire(&b->gen) == g) {
+                if (++i >= BARRIER_LIMIT) {
+                    atomicExch(&b->err, 1);
+                    ok = 0;
+                    break;
+                }
+                if (i > 64) __nanosleep(20);
+            }
+        }
+        s_ok = ok && *(volatile int *)&b->err == 0;
+        gen = g + 1;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// All nsteps RK4 steps of `count` fields in one cooperative launch: the four
+// stages of each step are grid-wide passes over every point, separated by
+// grid barriers (the per-stage arithmetic of rk4_stage_kernel, operand for
+// operand, so the two paths agree bitwise).  u holds the state (updated in
+// place at stage 4), y1/y2 the stage values, acc the running increment sum.
+// The per-stage weights of every field are computed in FP64 once per step
+// per block (count <= PERSIST_MAX_FIELDS).  For grids small enough that a
+// step is a few microseconds of work, this replaces 4 launches per step by
+// 4 barriers.
+template <typename T, int R>
+__global__ void __launch_bounds__(256)
+rk4_persist_kernel(StepArgs a, T *__restrict__ u, T *__restrict__ y1, T *__restrict__ y2,
+                   T *__restrict__ acc, long long nsteps, GridBarrier *bar)
+{
+    constexpr int NW = 1 + 6 * R;
+    __shared__ T sw[PERSIST_MAX_FIELDS * 4 * NW];
+    unsigned gen = *(volatile unsigned *)&bar->gen;
+    const int n = a.n;
+    const long long nn = (long long)n * n;
+    const long long total = (long long)a.count * a.P;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    auto wrap = [n](int i, int k) { i += k; return i < 0 ? i + n : (i >= n ? i - n : i); };
+    for (long long j = 0; j < nsteps; ++j) {
+        __syncthreads();      // the previous step's readers of sw are done
+        for (int i = threadIdx.x; i < a.count * 4; i += blockDim.x) {
+            const int f = i / 4, stage = i % 4 + 1;
+            const long long s = (long long)(a.first_slice + f * a.slice_stride) * a.steps_per_slice + j;
+            const double t = (double)s * a.dt;
+            const double c = (stage <= 1 || a.frozen) ? 0.0 : (stage == 4 ? 1.0 : 0.5);
+            double w[13];
+            op_weights(a.op, nu_at(a, t + c * a.dt), a.dt, n, a.a, w);
+            for (int k = 0; k < NW; ++k) sw[i * NW + k] = (T)w[k];
+        }
+        __syncthreads();
+        for (int stage = 1; stage <= 4; ++stage) {
+            const T *ys = stage == 1 ? u : (stage == 3 ? y2 : y1);
+            T *yd = stage == 2 ? y2 : y1;
+            for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
+                const int f = (int)(q / a.P);
+                const long long p = q - (long long)f * a.P;
+                const T *w = sw + (f * 4 + stage - 1) * NW;
+                const int x = (int)(p % n), y = (int)((p / n) % n), z = (int)(p / nn);
+                const T *Y = ys + (long long)f * a.P;
+                const long long row = (long long)z * nn + (long long)y * n;
+                T d = w[0] * Y[row + x];
+#pragma unroll
+                for (int r = 1; r <= R; ++r) {
+                    const int b = 1 + 6 * (r - 1);
+                    d = fma(w[b + 0], Y[row + wrap(x, -r)], d);
+                    d = fma(w[b + 1], Y[row + wrap(x, r)], d);
+                    d = fma(w[b + 2], Y[(long long)z * nn + (long long)wrap(y, -r) * n + x], d);
+                    d = fma(w[b + 3], Y[(long long)z * nn + (long long)wrap(y, r) * n + x], d);
+                    d = fma(w[b + 4], Y[(long long)wrap(z, -r) * nn + (long long)y * n + x], d);
+                    d = fma(w[b + 5], Y[(long long)wrap(z, r) * nn + (long long)y * n + x], d);
+                }
+                const T uq = u[q];
+                if (stage == 1) {
+                    yd[q] = fma((T)0.5, d, uq);
+                    acc[q] = d * (T)(1.0 / 6.0);
+                } else if (stage == 2) {
+                    yd[q] = fma((T)0.5, d, uq);
+                    acc[q] = fma((T)(1.0 / 3.0), d, acc[q]);
+                } else if (stage == 3) {
+                    yd[q] = uq + d;
+                    acc[q] = fma((T)(1.0 / 3.0), d, acc[q]);
+                } else {
+                    u[q] = uq + fma((T)(1.0 / 6.0), d, acc[q]);
+                }
+            }
+            if (j == nsteps - 1 && stage == 4) break;      // the launch's end is the last barrier
+            if (!grid_sync_bounded(bar, gridDim.x, gen)) return;
+        }
+    }
+}
+
+// Failure-detection self-test of the grid barrier: block 0 leaves without
+// arriving, so every other block's wait must give up and set the flag.
+__global__ void grid_barrier_selftest_kernel(GridBarrier *b)
+{
+    unsigned gen = *(volatile unsigned *)&b->gen;
+    if (blockIdx.x == 0) return;
+    grid_sync_bounded(b, gridDim.x, gen);
+}
+
+cudaError_t launch_grid_barrier_selftest(GridBarrier *b, cudaStream_t st)
+{
+    void *args[] = {&b};
+    return cudaLaunchCooperativeKernel((const void *)grid_barrier_selftest_kernel, dim3(sm_count()),
+                                       dim3(32), args, 0, st);
+}
+
+template <typename T, int R>
+static int persist_grid()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rk4_persist_kernel<T, R>, 256, 0) !=
+            cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int g = per_sm * sm_count();
+    if (dev >= 0 && dev < 64) cached[dev] = g;
+    return g;
+}
+
+template <typename T>
+cudaError_t launch_rk4_persist(const StepArgs &a0, T *u, T *y1, T *y2, T *acc, long long nsteps,
+                               GridBarrier *bar, cudaStream_t st)
+{
+    if (nsteps <= 0) return cudaSuccess;
+    for (int f0 = 0; f0 < a0.count; f0 += PERSIST_MAX_FIELDS) {
+        StepArgs a = a0;
+        a.count = a0.count - f0 < PERSIST_MAX_FIELDS ? a0.count - f0 : PERSIST_MAX_FIELDS;
+        a.first_slice = a0.first_slice + f0 * a0.slice_stride;
+        a.j = 0;
+        const long long off = (long long)f0 * a0.P;
+        T *pu = u + off, *p1 = y1 + off, *p2 = y2 + off, *pa = acc + off;
+        const long long total = (long long)a.count * a.P;
+        const bool r2 = op_radius(a.op) == 2;
+        const int cap = r2 ? persist_grid<T, 2>() : persist_grid<T, 1>();
+        // one block per SM at least: the stage work is FP64-rate bound, so every
+        // SM takes a share even when that leaves threads idle
+        long long want = (total + 255) / 256;
+        if (want < sm_count()) want = sm_count();
+        const int grid = (int)(want < cap ? want : cap);
+        void *args[] = {&a, &pu, &p1, &p2, &pa, &nsteps, &bar};
+        const void *fn = r2 ? (const void *)rk4_persist_kernel<T, 2> : (const void *)rk4_persist_kernel<T, 1>;
+        const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, 0, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+template cudaError_t launch_rk4_persist<float>(const StepArgs &, float *, float *, float *, float *,
+                                               long long, GridBarrier *, cudaStream_t);
+template cudaError_t launch_rk4_persist<double>(const StepArgs &, double *, double *, double *,
+                                                double *, long long, GridBarrier *, cudaStream_t);
+
 // ------------------------------------------------- conversion, restriction
 
 __global__ void convert_d2f_kernel(const double *__restrict__ s, float *__restrict__ d, long long N)

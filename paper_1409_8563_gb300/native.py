@@ -116,6 +116,7 @@ SIGNATURES = {
     "parareal_profile_read": (_i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]),
     "parareal_launch_count": (ctypes.c_longlong, [_vp]),
     "parareal_selftest_timeout": (_i, [_vp]),
+    "parareal_selftest_grid_barrier": (_i, [_vp]),
     "parareal_save_state": (_i, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "parareal_load_state": (_i, [_vp, _vp, ctypes.c_size_t]),
     "parareal_last_error": (_cp, [_vp]),
@@ -161,6 +162,11 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def selftest_grid_barrier(stream=None):
+    """Run the persistent kernel's bounded grid-barrier self-test; returns the status."""
+    return int(lib().parareal_selftest_grid_barrier(_stream_ptr(stream)))
 
 
 def selftest_timeout(stream=None):

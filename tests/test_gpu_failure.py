@@ -31,3 +31,25 @@ def test_bounded_wait_gives_up_and_the_device_stays_usable():
     ctx.close()
     # and the self-test is repeatable on the same device
     assert native.selftest_timeout() == native.E_TIMEOUT
+
+
+def test_grid_barrier_gives_up_and_the_device_stays_usable():
+    """The persistent RK4 path's grid barrier with one block that never
+    arrives: the other blocks' bounded waits give up, the host reads
+    PARAREAL_E_TIMEOUT, and an FP64 context on the persistent path still
+    matches the oracle afterwards."""
+    t0 = time.perf_counter()
+    st = native.selftest_grid_barrier()
+    took = time.perf_counter() - t0
+    assert st == native.E_TIMEOUT, st
+    assert "self-test" in native.lib().parareal_last_error(None).decode()
+    assert took < 30.0, took
+    cfg, u0 = configs.small(n=16, n_slices=2, dtype=native.F64, nf=4, nc=2)
+    ctx = native.Parareal(cfg)
+    assert ctx.launch_shape()[0][0] == 3          # the persistent path
+    src = torch.from_numpy(np.ascontiguousarray(u0[None])).cuda()
+    dst = torch.empty_like(src)
+    ctx.propagate(0, src, dst, 0, 1)
+    assert rel_l2(dst[0].cpu().numpy(), oracle_F(cfg)(u0, 0)) < TOL[native.F64]
+    ctx.close()
+    assert native.selftest_grid_barrier() == native.E_TIMEOUT

@@ -41,7 +41,7 @@ def small_cfg(n, n_slices, dtype, a=(1.0, 1.0, 1.0), omega=100.0):
 def test_c4_fine_propagator_matches_oracle(n, dtype):
     cfg = small_cfg(n, 4, dtype)
     ctx = native.Parareal(cfg)
-    assert ctx.launch_shape()[0][0] == 1        # the per-stage kernels
+    assert ctx.launch_shape()[0][0] in (1, 3)   # per-stage arithmetic: staged or persistent
     src = np.stack([inputs.spectral_ic(n, seed=30 + s, kmax=n // 4) for s in range(3)])
     dsrc = dev(src, dtype)
     ddst = torch.empty_like(dsrc)
