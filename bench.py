@@ -475,6 +475,9 @@ def run(args):
     torch.cuda.empty_cache()
     if rank == 0 and world == 1 and args.workload == "fp32_256" and not args.no_c4:
         line["c4_learned_128"] = c4_learned_128(local)
+    if rank == 0 and world == 1 and args.workload == "fp32_256" and not args.no_c3:
+        line["c3_batch64"] = {m: batch64(args.correction, m == "queue", 1, 1)
+                              for m in ("graph", "queue")}
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -872,22 +875,26 @@ def run_learned_g(args):
     return 0
 
 
-def run_batch64(args):
+def batch64(correction="difference", queue=False, steps=1, warmup=1):
     """64 uneven instances (sizes from {32,48,64,96,128}, nu0 in [0.002, 0.02],
-    N = 8, T = 1): one CUDA graph per round; autotuned launch shapes."""
+    N = 8, T = 1) solved to a defect of 1e-6: one CUDA graph per round, the
+    fine sweeps as each instance's own launches (graph mode) or as one
+    persistent launch over a queue of every instance's tile steps (queue
+    mode); autotuned launch shapes.  serial_fine_ms: every instance's serial
+    fine run, all instances concurrently."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_1409_8563_gb300 import configs, inputs, native
     ns, nus = inputs.batch_instances(seed=0)
     cfgs, u0s = [], []
     for i, (n, nu0) in enumerate(zip(ns, nus)):
         cfg, u0 = configs.batch_instance(n, nu0, seed=i)
-        cfg.correction_form = (native.CORRECTION_DIFFERENCE if args.correction == "difference"
+        cfg.correction_form = (native.CORRECTION_DIFFERENCE if correction == "difference"
                                else native.CORRECTION_STANDARD)
         cfgs.append(cfg)
         u0s.append(torch.from_numpy(u0).cuda())
     b = native.Batch(cfgs)
+    if queue:
+        b.set_fine_mode(1)
     tune_ms, _ = _timed(lambda: b.autotune(os.path.join(ROOT, "paper_1409_8563_gb300", "tune_cache.jsonl")))
     for i, u in enumerate(u0s):
         b.set_problem(i, u)
@@ -898,18 +905,30 @@ def run_batch64(args):
         for i, u in enumerate(u0s):
             b.set_problem(i, u)
         return b.iterate(8, TOL, native.STOP_DEFECT)
-    solve()
-    ms, (k, d) = _timed(solve, args.steps)
+    for _ in range(max(warmup, 1)):
+        solve()
+    ms, (k, d) = _timed(solve, max(steps, 1))
     ups = 0
     for cfg, kk in zip(cfgs, k):
         nf = round(cfg.T / cfg.n_slices / cfg.dt_fine)
         ups += sum(cfg.n_slices - j for j in range(int(kk))) * cfg.n ** 3 * nf
-    print(json.dumps({"workload": "batch64", "time_to_1e-6_ms": ms, "serial_fine_ms": serial_ms,
-                      "k_star": [int(x) for x in k], "max_defect": float(max(d)),
-                      "glups_in_solve": ups / ms / 1e6, "autotune_ms": tune_ms,
-                      "correction_form": args.correction,
-                      "graph_launches": b.graph_launches()}))
+    out = {"workload": "batch64", "fine_mode": "queue" if queue else "graph",
+           "time_to_1e-6_ms": ms, "serial_fine_ms": serial_ms,
+           "parareal_over_serial": ms / serial_ms,
+           "k_star": [int(x) for x in k], "max_defect": float(max(d)),
+           "glups_in_solve": ups / ms / 1e6, "autotune_ms": tune_ms,
+           "correction_form": correction, "fine_shape": list(b.fine_mode()),
+           "graph_launches": b.graph_launches()}
     b.close()
+    del u0s
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch64(args):
+    import __graft_entry__
+    __graft_entry__.build()
+    print(json.dumps(batch64(args.correction, args.queue, args.steps, args.warmup)))
     return 0
 
 
@@ -957,6 +976,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="fp32_256: leave out the 64-instance batch comparison (graph and queue modes)")
     ap.add_argument("--no-c4", action="store_true",
                     help="skip the 128^3 learned-propagator comparison of the default line")
     ap.add_argument("--workload", default="fp32_256",
@@ -965,6 +986,9 @@ def main():
     ap.add_argument("--slices", type=int, default=8)
     ap.add_argument("--correction", default="difference", choices=["difference", "standard"],
                     help="evaluation of the Parareal correction (fp32_256 / fp32_128 / batch64)")
+    ap.add_argument("--queue", action="store_true",
+                    help="batch64: the fine sweeps of a round as one persistent launch over a "
+                         "queue of every instance's tile steps")
     ap.add_argument("--transfer", default="box", choices=["box", "spectral"],
                     help="fp32_256 / fp32_128: restriction and prolongation of the coarse "
                          "propagator (box + trilinear, or spectral)")

@@ -352,6 +352,30 @@ parareal_status parareal_batch_iterate(parareal_batch *b, int k_max, double tol,
                                        int *k_done, double *defect);
 /* Autotune once per distinct (n, n/coarse_factor, dtype, N_p); call before set_problem. */
 parareal_status parareal_batch_autotune(parareal_batch *b, const char *cache_path);
+/* How the fine sweeps of a round run.  mode 0 (default): each instance's own
+ * batched launches, in its branch of the round's graph.  mode 1: ONE
+ * persistent launch over a queue of every open instance's tile steps (all
+ * steps, all slices, all tiles, in step order), with tile_x x tile_y tiles
+ * and `rows` region rows per thread for every instance (a tile that reaches
+ * past a grid's edge wraps and writes only its own points); CTAs take the
+ * next tile step from a device counter, and a step of instance i waits
+ * (bounded) until every tile of i's previous step is done.  The coarse
+ * sweeps and corrections then run as the graph's per-instance branches.
+ * In mode 1 every instance's own fine launches (its fine_sweep calls) take
+ * the queue's tile shape too; its serial fine run keeps its shape when that
+ * is a fused one and takes the queue's otherwise.  The fused tile step gives
+ * every point the same arithmetic whatever the shape, so the reference and
+ * the iterates share one arithmetic; an instance's iterates are then the
+ * same, bit for bit, as in mode 0 with fused fine shapes.
+ * mode 1 needs FP32 instances of the 7-point operator, at most 64, and one
+ * of the compiled shapes (64x32 and 64x16 with one row per thread, 32x16,
+ * 64x32 with two); parareal_batch_autotune then picks the shape by timing.
+ * A queue wait that gives up makes parareal_batch_iterate return
+ * PARAREAL_E_TIMEOUT.  No counterpart in the paper. */
+parareal_status parareal_batch_set_fine_mode(parareal_batch *b, int mode, int tile_x, int tile_y,
+                                             int rows);
+/* mode4 = {mode, tile_x, tile_y, rows} of parareal_batch_set_fine_mode. */
+parareal_status parareal_batch_get_fine_mode(const parareal_batch *b, int *mode4);
 /* The context of instance i (owned by the batch; use it for get_slice etc.). */
 parareal_ctx *parareal_batch_context(parareal_batch *b, int i);
 long long parareal_batch_graph_launches(const parareal_batch *b);

@@ -182,12 +182,20 @@ static void default_tiles(int dtype, int n, int count, int *path, int *tx, int *
     const int cand[][2] = {{64, 16}, {32, 16}, {32, 8}, {16, 16}};
     const int candd[][2] = {{32, 8}, {16, 16}, {16, 8}};
     *tx = *ty = 0;
+    // a tile that divides n; failing that (FP32), the one that wastes least
     if (dtype == PARAREAL_F32) {
         for (auto &t : cand)
-            if (rk4_fused_supported(dtype, n, t[0], t[1], 1)) { *tx = t[0]; *ty = t[1]; break; }
+            if (n % t[0] == 0 && n % t[1] == 0) { *tx = t[0]; *ty = t[1]; break; }
+        if (*tx == 0) {
+            long long best = -1;
+            for (auto &t : cand) {
+                const long long cover = (long long)((n + t[0] - 1) / t[0] * t[0]) * ((n + t[1] - 1) / t[1] * t[1]);
+                if (best < 0 || cover < best) { best = cover; *tx = t[0]; *ty = t[1]; }
+            }
+        }
     } else {
         for (auto &t : candd)
-            if (rk4_fused_supported(dtype, n, t[0], t[1], 1)) { *tx = t[0]; *ty = t[1]; break; }
+            if (n % t[0] == 0 && n % t[1] == 0) { *tx = t[0]; *ty = t[1]; break; }
     }
     if (*tx == 0) { *path = *path == PATH_PERSIST ? PATH_PERSIST : PATH_STAGED; *tx = 16; *ty = 8; }
     // z chunk: whole columns unless the launch would leave SMs idle
@@ -510,11 +518,16 @@ static parareal_status coarse_chain(parareal_ctx *c, int first, int count, bool 
 // fine sweep of slices K..N-1, then the serial coarse sweep with the
 // correction and per-slice norms, then (with a reference) the defect norms
 // into slot N+1 of slice_norms.  K = c->k_total: U[0..K] are already exact.
-parareal_status iter_enqueue(parareal_ctx *c, bool copy_norms)
+// with_fine = false leaves out the fine sweep (the caller has put F(U^k[n])
+// into Fv[n+1] another way); copy_norms = false leaves the norms on the device.
+parareal_status iter_enqueue(parareal_ctx *c, bool copy_norms, bool with_fine)
 {
     const int K = c->k_total;
-    parareal_status s = DISPATCH(c, fine_sweep_t, K, c->N - K);
-    if (s != PARAREAL_OK) return s;
+    parareal_status s = PARAREAL_OK;
+    if (with_fine) {
+        s = DISPATCH(c, fine_sweep_t, K, c->N - K);
+        if (s != PARAREAL_OK) return s;
+    }
     if (c->cfg.correction_form == PARAREAL_CORRECTION_DIFFERENCE) {
         // U[n+1] = Fv[n+1] + G(D_n), D_n = U^{k+1}[n] - U^k[n] (G linear); the
         // correction of slice n writes D_{n+1}.  D_K = 0: slice K+1 takes Fv alone.
@@ -612,7 +625,8 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, PARAREAL_E_CUDA, "no CUDA device");
         if (std::find(configured.begin(), configured.end(), dev) == configured.end()) {
-            if (configure_rk4_kernels() != cudaSuccess || configure_spectral_kernels() != cudaSuccess)
+            if (configure_rk4_kernels() != cudaSuccess || configure_spectral_kernels() != cudaSuccess ||
+                configure_queue_kernels() != cudaSuccess)
                 return fail(nullptr, PARAREAL_E_CUDA, "kernel configuration failed");
             configured.push_back(dev);
         }

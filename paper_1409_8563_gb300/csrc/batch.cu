@@ -9,12 +9,21 @@
 // the GPU schedules the small instances' kernels side by side.  After the
 // graph ran, one host pass reads every instance's norms and applies its
 // stopping rule.
+#include <algorithm>
+#include <cstring>
 #include <string>
 #include <vector>
 
 #include "ctx.cuh"
 
 struct parareal_batch {
+    // fine sweeps of a round: 0 = each instance's own launches in its graph
+    // branch; 1 = one persistent launch over a queue of every instance's tile
+    // steps (queue tile shape qtx x qty, qrows rows per thread)
+    int fine_mode = 0;
+    int qtx = 64, qty = 32, qrows = 1;
+    unsigned long long *qhead = nullptr, *qdone = nullptr;
+    int *qerr = nullptr;
     std::vector<parareal_ctx *> ctx;
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> join;
@@ -46,6 +55,9 @@ extern "C" void parareal_batch_destroy(parareal_batch *b)
     for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->join) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->qhead) cudaFree(b->qhead);
+    if (b->qdone) cudaFree(b->qdone);
+    if (b->qerr) cudaFree(b->qerr);
     if (b->own_main && b->main) cudaStreamDestroy(b->main);
     delete b;
 }
@@ -88,7 +100,164 @@ extern "C" parareal_status parareal_batch_create(const parareal_config *cfgs, in
         b->ctx.push_back(c);
     }
     b->stopped.assign(count, 0);
+    if (cudaMalloc((void **)&b->qhead, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc((void **)&b->qdone, sizeof(unsigned long long) * pr::QUEUE_MAX) != cudaSuccess ||
+        cudaMalloc((void **)&b->qerr, sizeof(int)) != cudaSuccess ||
+        cudaMemset(b->qerr, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        parareal_batch_destroy(b);
+        return PARAREAL_E_NOMEM;
+    }
     *out = b;
+    return PARAREAL_OK;
+}
+
+// The queue of one round: the fine sweep of the open slices of every
+// selected instance (steps and tiles as rk4_batch lays them out), entries
+// sorted by step count, longest first.  Input: each instance's U[K..N-1] in
+// FP32 in its wC (converted by the caller), output Fv[K+1..N].
+static void build_queue(parareal_batch *b, const std::vector<int> &sel, int nsteps_override,
+                        pr::QueueParams *q)
+{
+    std::vector<int> order(sel);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return b->ctx[x]->Nf > b->ctx[y]->Nf;
+    });
+    std::memset(q, 0, sizeof *q);
+    q->n_entries = (int)order.size();
+    q->items_prefix[0] = 0;
+    for (int k = 0; k < q->n_entries; ++k) {
+        parareal_ctx *c = b->ctx[order[k]];
+        pr::QueueEntry &E = q->e[k];
+        const int K = c->k_total;
+        pr::StepArgs &a = E.a;
+        a.op = pr::OP_C2;
+        a.n = c->n;
+        a.P = c->P;
+        a.count = c->N - K;
+        a.first_slice = K;
+        a.slice_stride = 1;
+        a.steps_per_slice = c->Nf;
+        a.dt = c->cfg.dt_fine;
+        for (int d = 0; d < 3; ++d) a.a[d] = c->cfg.a[d];
+        a.nu0 = c->cfg.nu0;
+        a.nu_amp = c->cfg.nu_amp;
+        a.nu_omega = c->cfg.nu_omega;
+        a.frozen = c->cfg.nu_mode == PARAREAL_NU_FROZEN;
+        E.in = static_cast<const float *>(c->wC);
+        E.out = static_cast<float *>(c->Fv) + (long long)(K + 1) * c->P;
+        E.ws1 = static_cast<float *>(c->wA);
+        E.ws2 = static_cast<float *>(c->wB);
+        E.nsteps = nsteps_override > 0 ? nsteps_override : c->Nf;
+        E.tiles_x = (c->n + b->qtx - 1) / b->qtx;
+        E.tiles_y = (c->n + b->qty - 1) / b->qty;
+        E.zchunk = c->n <= 64 ? c->n : 64;
+        E.nzc = (c->n + E.zchunk - 1) / E.zchunk;
+        E.items = (long long)a.count * E.tiles_x * E.tiles_y * E.nzc;
+        q->items_prefix[k + 1] = q->items_prefix[k] + E.items;
+    }
+    // segments of steps with the same active prefix of entries
+    q->n_segs = 0;
+    long long step = 0, item = 0;
+    for (int active = q->n_entries; active > 0; --active) {
+        const long long last = q->e[active - 1].nsteps;    // steps while `active` entries run
+        if (last <= step) continue;
+        q->seg_first_step[q->n_segs] = step;
+        q->seg_active[q->n_segs] = active;
+        q->seg_first_item[q->n_segs] = item;
+        item += (last - step) * q->items_prefix[active];
+        step = last;
+        ++q->n_segs;
+    }
+    q->seg_first_step[q->n_segs] = step;
+    q->seg_first_item[q->n_segs] = item;
+    q->total = item;
+}
+
+// Enqueue the queue launch of a round on b->main: zeroed counters, every
+// selected instance's U[K..N-1] converted to FP32 into its wC, one launch.
+static parareal_status enqueue_queue(parareal_batch *b, const std::vector<int> &sel, int nsteps_override)
+{
+    static pr::QueueParams q;      // ~14 KB: kept off the stack
+    build_queue(b, sel, nsteps_override, &q);
+    BK(cudaMemsetAsync(b->qhead, 0, sizeof(unsigned long long), b->main));
+    BK(cudaMemsetAsync(b->qdone, 0, sizeof(unsigned long long) * pr::QUEUE_MAX, b->main));
+    for (int i : sel) {
+        parareal_ctx *c = b->ctx[i];
+        const int K = c->k_total;
+        BK(pr::launch_convert_f64_to_f32(c->U + (long long)K * c->P, static_cast<float *>(c->wC),
+                                         (long long)(c->N - K) * c->P, b->main));
+        c->launches++;
+    }
+    BK(pr::launch_rk4_queue(q, b->qtx, b->qty, b->qrows, b->qhead, b->qdone, b->qerr, b->main));
+    return PARAREAL_OK;
+}
+
+// The queue's device-side waits since the last check.
+static parareal_status queue_check(parareal_batch *b)
+{
+    int h = 0;
+    BK(cudaMemcpyAsync(&h, b->qerr, sizeof h, cudaMemcpyDeviceToHost, b->main));
+    BK(cudaStreamSynchronize(b->main));
+    if (h) {
+        BK(cudaMemsetAsync(b->qerr, 0, sizeof h, b->main));
+        return bfail(b, PARAREAL_E_TIMEOUT, "a tile step of the batch queue gave up waiting for its problem's previous step");
+    }
+    return PARAREAL_OK;
+}
+
+// With the queue, every instance's batched and single-field fine launches
+// use the queue's tile shape too: the serial fine run (the reference) then
+// takes the same arithmetic as the queue's sweeps.
+// The instances' own fine launches take the queue's shape.  The fused tile
+// step computes every point by the same expression whatever the tile, rows
+// per thread or z chunk, so a serial sweep already on a fused shape (the
+// autotuned one) keeps it and its result stays bitwise the queue's; any
+// other serial path moves to the queue's shape.
+static void queue_shapes_to_instances(parareal_batch *b)
+{
+    const int path = b->qrows == 2 ? PATH_FUSED2 : PATH_FUSED;
+    for (parareal_ctx *c : b->ctx) {
+        c->fine_path = path;
+        c->fine_tx = b->qtx;
+        c->fine_ty = b->qty;
+        c->fine_zc = c->n <= 64 ? c->n : 64;
+        if (c->ser_path != PATH_FUSED && c->ser_path != PATH_FUSED2) {
+            c->ser_path = path;
+            c->ser_tx = b->qtx;
+            c->ser_ty = b->qty;
+            c->ser_zc = c->fine_zc;
+        }
+    }
+}
+
+extern "C" parareal_status parareal_batch_set_fine_mode(parareal_batch *b, int mode, int tile_x,
+                                                         int tile_y, int rows)
+{
+    if (!b || (mode != 0 && mode != 1)) return PARAREAL_E_INVALID;
+    if (mode == 1) {
+        if ((int)b->ctx.size() > pr::QUEUE_MAX) return bfail(b, PARAREAL_E_INVALID, "at most 64 instances in the queue");
+        if (!pr::rk4_queue_supported(tile_x, tile_y, rows))
+            return bfail(b, PARAREAL_E_INVALID, "tile shape not compiled for the queue");
+        for (parareal_ctx *c : b->ctx)
+            if (c->f64 || c->fine_op != pr::OP_C2)
+                return bfail(b, PARAREAL_E_INVALID, "the queue runs FP32 instances of the 7-point operator");
+        b->qtx = tile_x;
+        b->qty = tile_y;
+        b->qrows = rows;
+        queue_shapes_to_instances(b);
+    }
+    b->fine_mode = mode;
+    return PARAREAL_OK;
+}
+
+extern "C" parareal_status parareal_batch_get_fine_mode(const parareal_batch *b, int *mode4)
+{
+    if (!b || !mode4) return PARAREAL_E_INVALID;
+    mode4[0] = b->fine_mode;
+    mode4[1] = b->qtx;
+    mode4[2] = b->qty;
+    mode4[3] = b->qrows;
     return PARAREAL_OK;
 }
 
@@ -132,11 +301,13 @@ extern "C" parareal_status parareal_batch_serial_fine(parareal_batch *b, int as_
 // Capture fn(ctx) for every selected instance as parallel branches of one
 // graph on b->main, then launch it and wait.
 template <typename Fn>
-static parareal_status run_round(parareal_batch *b, const std::vector<int> &sel, Fn fn)
+static parareal_status run_round(parareal_batch *b, const std::vector<int> &sel, Fn fn,
+                                 bool queue = false)
 {
     if (sel.empty()) return PARAREAL_OK;
     BK(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal));
-    parareal_status s = PARAREAL_OK;
+    // the fine sweeps of every selected instance first, as one queue launch
+    parareal_status s = queue ? enqueue_queue(b, sel, 0) : PARAREAL_OK;
     cudaError_t ce = cudaEventRecord(b->fork, b->main);
     for (size_t q = 0; q < sel.size() && s == PARAREAL_OK && ce == cudaSuccess; ++q) {
         const int i = sel[q];
@@ -167,7 +338,7 @@ static parareal_status run_round(parareal_batch *b, const std::vector<int> &sel,
     cudaGraphExecDestroy(x);
     if (se != cudaSuccess) return bfail(b, PARAREAL_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(se));
     b->graph_launches++;
-    return PARAREAL_OK;
+    return queue ? queue_check(b) : PARAREAL_OK;
 }
 
 extern "C" parareal_status parareal_batch_iterate(parareal_batch *b, int k_max, double tol,
@@ -197,7 +368,9 @@ extern "C" parareal_status parareal_batch_iterate(parareal_batch *b, int k_max, 
         for (int i = 0; i < M; ++i)
             if (!b->stopped[i] && b->ctx[i]->k_total < b->ctx[i]->N) sel.push_back(i);
         if (sel.empty()) break;
-        s = run_round(b, sel, [](parareal_ctx *c) { return iter_enqueue(c); });
+        const bool queue = b->fine_mode == 1;
+        s = run_round(b, sel, [queue](parareal_ctx *c) { return iter_enqueue(c, true, !queue); },
+                      queue);
         if (s != PARAREAL_OK) return s;
         for (int i : sel) {
             parareal_ctx *c = b->ctx[i];
@@ -238,6 +411,50 @@ extern "C" parareal_status parareal_batch_autotune(parareal_batch *b, const char
         c->coarse_ty = same->coarse_ty; c->coarse_zc = same->coarse_zc;
         c->has_problem = false;
         c->started = false;
+    }
+    if (b->fine_mode == 1) {
+        // the queue's tile shape: two steps of every instance's full sweep per
+        // candidate, timed with events (best of three after a warm-up)
+        std::vector<int> all;
+        for (int i = 0; i < (int)b->ctx.size(); ++i) {
+            b->ctx[i]->k_total = 0;
+            all.push_back(i);
+        }
+        const int shapes[][3] = {{64, 32, 1}, {64, 16, 1}, {32, 16, 1}, {64, 32, 2}};
+        cudaEvent_t e0, e1;
+        BK(cudaEventCreate(&e0));
+        BK(cudaEventCreate(&e1));
+        double best = 1e30;
+        int pick = 0;
+        for (int k = 0; k < 4; ++k) {
+            b->qtx = shapes[k][0];
+            b->qty = shapes[k][1];
+            b->qrows = shapes[k][2];
+            double t_best = 1e30;
+            for (int trial = 0; trial < 4; ++trial) {
+                BK(cudaEventRecord(e0, b->main));
+                parareal_status s = enqueue_queue(b, all, 2);
+                if (s != PARAREAL_OK) return s;
+                BK(cudaEventRecord(e1, b->main));
+                BK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                BK(cudaEventElapsedTime(&ms, e0, e1));
+                if (trial > 0) t_best = std::min(t_best, (double)ms);
+            }
+            parareal_status s = queue_check(b);
+            if (s != PARAREAL_OK) return s;
+            if (t_best < best) { best = t_best; pick = k; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        b->qtx = shapes[pick][0];
+        b->qty = shapes[pick][1];
+        b->qrows = shapes[pick][2];
+        queue_shapes_to_instances(b);
+        for (parareal_ctx *c : b->ctx) {
+            c->has_problem = false;
+            c->started = false;
+        }
     }
     return PARAREAL_OK;
 }

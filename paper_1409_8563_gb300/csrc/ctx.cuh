@@ -143,7 +143,7 @@ parareal_status euler_batch(parareal_ctx *c, int m, const T *in, T *out, int fir
                             int count, long long nsteps, double dt, int op, T *ws1, T *ws2);
 
 // api.cu: one Parareal iteration split into device work and host bookkeeping
-parareal_status iter_enqueue(parareal_ctx *c, bool copy_norms = true);
+parareal_status iter_enqueue(parareal_ctx *c, bool copy_norms = true, bool with_fine = true);
 parareal_status iter_finish(parareal_ctx *c, double *dmax, double *l2max, double *d);
 
 // api.cu: the stencil coarse propagator of slice s, prolonged to the fine

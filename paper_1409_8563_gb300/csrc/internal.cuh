@@ -95,7 +95,8 @@ int sm_count();
 // All launchers enqueue on `st` and return cudaGetLastError().
 
 // Fused z-marching RK4 step (one full step per launch, all stages on chip);
-// `rows` = region rows per thread (1 or 2).
+// `rows` = region rows per thread (1 or 2).  The tile need not divide n:
+// tiles at the grid's edge wrap periodically and write only their own points.
 template <typename T>
 cudaError_t launch_rk4_fused(const StepArgs &a, const T *in, T *out, int tile_x, int tile_y,
                              int zchunk, int rows, cudaStream_t st);
@@ -109,6 +110,35 @@ cudaError_t configure_rk4_kernels();
 template <typename T>
 cudaError_t launch_rk4_stage(const StepArgs &a, int stage, const T *ysrc, T *u, T *ydst,
                              T *acc, cudaStream_t st);
+
+// A batch of independent problems' fine sweeps of one Parareal round as one
+// persistent launch over a queue of tile steps (launch_rk4_queue).  Entry i
+// is the batched RK4 sweep of one problem: a.count fields of a.n^3 points,
+// nsteps steps from `in` into `out` through ws1/ws2 (the ping-pong of
+// rk4_batch), tiles of the queue's shape with z chunks of zchunk planes.
+struct QueueEntry {
+    StepArgs a;
+    const float *in;
+    float *out, *ws1, *ws2;
+    long long nsteps;
+    int tiles_x, tiles_y, nzc, zchunk;
+    long long items;                  // tiles of one step: count * tiles_x * tiles_y * nzc
+};
+// Queue order: step by step; within a step the problems still stepping, in
+// entry order (entries sorted by nsteps, longest first, so the problems
+// active at step j are a prefix).  seg_first_step[s] .. [s+1] are the steps
+// with `seg_active[s]` problems; items_prefix[i] sums the items of entries
+// 0..i-1.
+constexpr int QUEUE_MAX = 64;
+struct QueueParams {
+    QueueEntry e[QUEUE_MAX];
+    int n_entries, n_segs;
+    long long seg_first_step[QUEUE_MAX + 1];
+    int seg_active[QUEUE_MAX];
+    long long seg_first_item[QUEUE_MAX + 1];
+    long long items_prefix[QUEUE_MAX + 1];
+    long long total;
+};
 
 // Grid-wide barrier state of the persistent RK4 kernel (device memory,
 // zero-initialised; err becomes 1 when a barrier wait gave up).
@@ -129,6 +159,18 @@ cudaError_t launch_rk4_persist(const StepArgs &a, T *u, T *y1, T *y2, T *acc, lo
 // Self-test: a cooperative launch in which one block never reaches the grid
 // barrier (every other block's bounded wait gives up and sets b->err).
 cudaError_t launch_grid_barrier_selftest(GridBarrier *b, cudaStream_t st);
+
+// The fine sweeps of up to QUEUE_MAX problems in one launch: CTAs take tile
+// steps from the queue in order (head: a device counter, zeroed before the
+// launch); a step of problem i waits, bounded, until done[i] counts every
+// tile of the problem's previous step (done zeroed before the launch; err
+// set when a wait gives up, after which the CTA stops).  FP32, the fused
+// kernel's tile arithmetic, so each field's result equals launch_rk4_fused's.
+cudaError_t launch_rk4_queue(const QueueParams &q, int tile_x, int tile_y, int rows,
+                             unsigned long long *head, unsigned long long *done, int *err,
+                             cudaStream_t st);
+bool rk4_queue_supported(int tile_x, int tile_y, int rows);
+cudaError_t configure_queue_kernels();
 
 // Elementwise conversions / copies of a batch of fields.
 cudaError_t launch_convert_f64_to_f32(const double *src, float *dst, long long count,

@@ -343,10 +343,15 @@ __device__ __forceinline__ void fused_step(FusedIter<T, R> &I, FusedRegs<T, R> &
 // With R = 2 a thread's own rows are each other's y neighbours, so per
 // stage it reads one shared-memory row above and one below for two rows of
 // results: a quarter less shared-memory traffic per point than R = 1.
+// The RK4 step of one tile column (tile tx, ty of field f, z chunk zc) by one
+// CTA of FusedShape::NT threads in the dynamic shared memory smem_raw.  A
+// tile that reaches past the grid's edge (n not a multiple of the tile)
+// wraps periodically like the halo and writes only the points of its own
+// [tx TX, min((tx+1) TX, n)) x [ty TY, ...) range.
 template <typename T, int TX, int TY, int R>
-__global__ void __launch_bounds__(FusedShape<T, TX, TY, R>::NT, FusedShape<T, TX, TY, R>::MINB)
-rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int tiles_x,
-                 int tiles_y, int zchunk, int nzc)
+__device__ __forceinline__ void fused_tile_step(const StepArgs &a, const T *__restrict__ in,
+                                                T *__restrict__ out, int f, int tx, int ty, int zc,
+                                                int zchunk, unsigned char *smem_raw)
 {
     using S = FusedShape<T, TX, TY, R>;
     constexpr int V = S::V, RX = S::RX, RY = S::RY, QX = S::QX, PL = S::PL, EL = S::EL;
@@ -354,7 +359,6 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
     constexpr int H = 4 / R;                       // halo row groups per side
     constexpr int RG = RY / R;                     // row groups in the region
     static_assert(TY % R == 0 && 4 % R == 0, "row groups must tile the region");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *ring = reinterpret_cast<T *>(smem_raw);
     T *planes = ring + RING * PL;
     T *ering = planes + 6 * PL;
@@ -371,11 +375,6 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
     const int hj = gi - TY / R;
     const int grp = gi < TY / R ? H + gi : ((hj & 1) ? RG - H + (hj >> 1) : H - 1 - (hj >> 1));
     const int ry = grp * R;                        // first region row of this thread
-    int b = blockIdx.x;
-    const int zc = b % nzc; b /= nzc;
-    const int tx = b % tiles_x; b /= tiles_x;
-    const int ty = b % tiles_y; b /= tiles_y;
-    const int f = b;
     const int n = a.n;
 
     if (tid < 3) {
@@ -448,7 +447,10 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
     I.act4 = __any_sync(lanes, active(4));
     // the region's inner rows [4, 4+TY) are whole row groups (4 and TY are
     // multiples of R), so a thread owns outputs in all of its rows or none
-    I.owner = ry >= 4 && ry < 4 + TY && qx * V >= 4 && qx * V < 4 + TX;
+    // (n is a multiple of 4, so the edge of a wrapped tile falls between row
+    // groups and between vectors)
+    I.owner = ry >= 4 && ry < 4 + TY && qx * V >= 4 && qx * V < 4 + TX &&
+              tx * TX + qx * V - 4 < n && ty * TY + ry - 4 < n;
 
     // prologue: planes of iterations 0 .. D-1 into ring slots 0 .. D-1
     int z0 = z_lo - 4;
@@ -493,11 +495,148 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
 }
 
 template <typename T, int TX, int TY, int R>
+__global__ void __launch_bounds__(FusedShape<T, TX, TY, R>::NT, FusedShape<T, TX, TY, R>::MINB)
+rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int tiles_x,
+                 int tiles_y, int zchunk, int nzc)
+{
+    extern __shared__ __align__(16) unsigned char smem_fused[];
+    int b = blockIdx.x;
+    const int zc = b % nzc; b /= nzc;
+    const int tx = b % tiles_x; b /= tiles_x;
+    const int ty = b % tiles_y; b /= tiles_y;
+    fused_tile_step<T, TX, TY, R>(a, in, out, b, tx, ty, zc, zchunk, smem_fused);
+}
+
+// ------------------------------------------------------- tile-step queue
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_add_release_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("red.add.release.gpu.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+constexpr long long QUEUE_WAIT_LIMIT = 1ll << 22;
+
+// Persistent CTAs that take the batch's tile steps from the queue in order.
+// An item only waits for items taken before it (its problem's previous
+// step), so the queue drains whatever the number of resident CTAs.
+template <int TX, int TY, int R>
+__global__ void __launch_bounds__(FusedShape<float, TX, TY, R>::NT, 1)
+rk4_queue_kernel(const __grid_constant__ QueueParams q, unsigned long long *head,
+                 unsigned long long *done, int *err)
+{
+    extern __shared__ __align__(16) unsigned char smem_queue[];
+    __shared__ long long s_item;
+    __shared__ int s_ok;
+    int seg = 0;                      // the item order only grows: cursors move forward
+    for (;;) {
+        __syncthreads();              // the previous item's threads are all done
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(head, 1ull);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= q.total) break;
+        while (seg + 1 < q.n_segs && q.seg_first_item[seg + 1] <= item) ++seg;
+        const long long per_step = q.items_prefix[q.seg_active[seg]];
+        const long long rel = item - q.seg_first_item[seg];
+        const long long j = q.seg_first_step[seg] + rel / per_step;
+        const long long r = rel % per_step;
+        int i = 0;
+        while (q.items_prefix[i + 1] <= r) ++i;
+        const QueueEntry &E = q.e[i];
+        long long local = r - q.items_prefix[i];
+        // the problem's previous step must be complete
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            const unsigned long long need = (unsigned long long)(j * E.items);
+            long long it = 0;
+            while (ld_acquire_u64(&done[i]) < need) {
+                if (++it >= QUEUE_WAIT_LIMIT || *(volatile int *)err) {
+                    atomicExch(err, 1);
+                    ok = 0;
+                    break;
+                }
+                if (it > 64) __nanosleep(64);
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        const int zc = (int)(local % E.nzc); local /= E.nzc;
+        const int tx = (int)(local % E.tiles_x); local /= E.tiles_x;
+        const int ty = (int)(local % E.tiles_y); local /= E.tiles_y;
+        const int f = (int)local;
+        StepArgs a = E.a;
+        a.j = j;
+        const float *src = j == 0 ? E.in : ((j - 1) & 1 ? E.ws2 : E.ws1);
+        float *dst = j == E.nsteps - 1 ? E.out : ((j & 1) ? E.ws2 : E.ws1);
+        fused_tile_step<float, TX, TY, R>(a, src, dst, f, tx, ty, zc, E.zchunk, smem_queue);
+        __syncthreads();              // every thread's stores of this tile precede the release
+        if (threadIdx.x == 0) red_add_release_u64(&done[i], 1ull);
+    }
+}
+
+#define PR_QUEUE_SHAPES(X) \
+    X(64, 32, 1)           \
+    X(64, 16, 1)           \
+    X(32, 16, 1)           \
+    X(64, 32, 2)
+
+cudaError_t configure_queue_kernels()
+{
+    cudaError_t e = cudaSuccess;
+#define PR_QCONF(TX, TY, R)                                                                      \
+    if (e == cudaSuccess)                                                                        \
+        e = cudaFuncSetAttribute(rk4_queue_kernel<TX, TY, R>,                                    \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,                    \
+                                 (int)FusedShape<float, TX, TY, R>::SMEM);
+    PR_QUEUE_SHAPES(PR_QCONF)
+#undef PR_QCONF
+    return e;
+}
+
+bool rk4_queue_supported(int tile_x, int tile_y, int rows)
+{
+#define PR_QSUP(TX, TY, R) \
+    if (tile_x == TX && tile_y == TY && rows == R) return true;
+    PR_QUEUE_SHAPES(PR_QSUP)
+#undef PR_QSUP
+    return false;
+}
+
+cudaError_t launch_rk4_queue(const QueueParams &q, int tile_x, int tile_y, int rows,
+                             unsigned long long *head, unsigned long long *done, int *err,
+                             cudaStream_t st)
+{
+    if (q.total <= 0) return cudaSuccess;
+#define PR_QLAUNCH(TX, TY, R)                                                                    \
+    if (tile_x == TX && tile_y == TY && rows == R) {                                             \
+        using S = FusedShape<float, TX, TY, R>;                                                  \
+        int per_sm = 0;                                                                          \
+        cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(                          \
+            &per_sm, rk4_queue_kernel<TX, TY, R>, S::NT, S::SMEM);                               \
+        if (oe != cudaSuccess) return oe;                                                        \
+        long long grid = (long long)(per_sm < 1 ? 1 : per_sm) * sm_count();                     \
+        if (grid > q.total) grid = q.total;                                                      \
+        rk4_queue_kernel<TX, TY, R><<<(unsigned)grid, S::NT, S::SMEM, st>>>(q, head, done, err);  \
+        return cudaGetLastError();                                                               \
+    }
+    PR_QUEUE_SHAPES(PR_QLAUNCH)
+#undef PR_QLAUNCH
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, int TX, int TY, int R>
 static cudaError_t launch_fused_shape(const StepArgs &a, const T *in, T *out, int zchunk,
                                       cudaStream_t st)
 {
     using S = FusedShape<T, TX, TY, R>;
-    const int tiles_x = a.n / TX, tiles_y = a.n / TY;
+    // a tile that reaches past the grid's edge wraps and owns only its part
+    const int tiles_x = (a.n + TX - 1) / TX, tiles_y = (a.n + TY - 1) / TY;
     const int nzc = (a.n + zchunk - 1) / zchunk;
     const long long blocks = (long long)a.count * tiles_x * tiles_y * nzc;
     rk4_fused_kernel<T, TX, TY, R><<<(unsigned)blocks, S::NT, S::SMEM, st>>>(a, in, out, tiles_x,
@@ -543,7 +682,7 @@ cudaError_t configure_rk4_kernels()
 
 bool rk4_fused_supported(int dtype, int n, int tile_x, int tile_y, int rows)
 {
-    if (n % tile_x || n % tile_y) return false;
+    if (n % 4) return false;
 #define PR_SUP(T, TX, TY, R)                                                                 \
     if ((dtype == PARAREAL_F64) == (sizeof(T) == 8) && tile_x == TX && tile_y == TY && rows == R) \
         return true;
@@ -556,7 +695,7 @@ template <typename T>
 cudaError_t launch_rk4_fused(const StepArgs &a, const T *in, T *out, int tile_x, int tile_y,
                              int zchunk, int rows, cudaStream_t st)
 {
-    if (zchunk <= 0 || a.n % tile_x || a.n % tile_y) return cudaErrorInvalidValue;
+    if (zchunk <= 0 || a.n % 4) return cudaErrorInvalidValue;
 #define PR_DISPATCH(TT, TX, TY, R)                                                          \
     if constexpr (std::is_same<T, TT>::value)                                                \
         if (tile_x == TX && tile_y == TY && rows == R)                                       \

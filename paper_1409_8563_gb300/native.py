@@ -106,6 +106,8 @@ SIGNATURES = {
     "parareal_batch_serial_fine": (_i, [_vp, _i]),
     "parareal_batch_iterate": (_i, [_vp, _i, _d, _i, _ip, _dp]),
     "parareal_batch_autotune": (_i, [_vp, _cp]),
+    "parareal_batch_set_fine_mode": (_i, [_vp, _i, _i, _i, _i]),
+    "parareal_batch_get_fine_mode": (_i, [_vp, _ip]),
     "parareal_batch_context": (_vp, [_vp, _i]),
     "parareal_batch_graph_launches": (ctypes.c_longlong, [_vp]),
     "parareal_batch_last_error": (_cp, [_vp]),
@@ -404,6 +406,16 @@ class Batch:
 
     def graph_launches(self):
         return int(lib().parareal_batch_graph_launches(self._h))
+
+    def set_fine_mode(self, mode, tile_x=64, tile_y=32, rows=1):
+        """mode 0: per-instance launches in graph branches; 1: one persistent
+        launch over a queue of every instance's tile steps."""
+        return self._check(lib().parareal_batch_set_fine_mode(self._h, mode, tile_x, tile_y, rows))
+
+    def fine_mode(self):
+        m = (ctypes.c_int * 4)()
+        self._check(lib().parareal_batch_get_fine_mode(self._h, m))
+        return tuple(m[:])
 
     def close(self):
         if self._h:

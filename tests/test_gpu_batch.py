@@ -114,3 +114,96 @@ def test_uneven_batch_of_64_instances_converges():
     assert np.all(d <= 1e-6), d
     assert np.all(k <= 8)
     b.close()
+
+
+def _all_slices(ctx, cfg):
+    a = torch.empty((cfg.n,) * 3, dtype=torch.float64, device="cuda")
+    out = []
+    for s in range(cfg.n_slices + 1):
+        ctx.get_slice(s, a)
+        out.append(a.cpu().numpy().copy())
+    return out
+
+
+@pytest.mark.parametrize("shape", [(64, 32, 1), (32, 16, 1), (64, 32, 2), (64, 16, 1)])
+def test_queue_round_matches_graph_round_bitwise(shape):
+    """Fine sweeps of a round as one persistent launch over the queue of every
+    instance's tile steps (uneven sizes, so uneven step counts and tiles
+    that wrap past the grid's edge): each instance's iterates equal those of
+    the per-instance graph branches, bit for bit, and the oracle's."""
+    cfgs, u0s = small_batch()
+    runs = []
+    for mode in (0, 1):
+        b = native.Batch(cfgs)
+        if mode:
+            b.set_fine_mode(1, *shape)
+            assert b.fine_mode() == (1,) + tuple(shape)
+        else:
+            fused = [b.context(i).launch_shape()[0][0] in (0, 2) for i in range(len(cfgs))]
+        for i, u0 in enumerate(u0s):
+            b.set_problem(i, torch.from_numpy(u0).cuda())
+        b.serial_fine(as_reference=True)
+        k, d = b.iterate(3, 0.0, native.STOP_NONE)
+        assert list(k) == [3] * len(cfgs)
+        runs.append(([_all_slices(b.context(i), c) for i, c in enumerate(cfgs)], d))
+        b.close()
+    (g, dg), (q, dq) = runs
+    # an instance that no fused tile divides (24^3) runs the per-stage kernels
+    # in the graph branches and the fused arithmetic in the queue: the same
+    # iteration within FP32 rounding; the others bit for bit
+    assert sum(fused) >= 3
+    for i, cfg in enumerate(cfgs):
+        if fused[i]:
+            assert dg[i] == dq[i], i
+        for s in range(cfg.n_slices + 1):
+            if fused[i]:
+                assert np.array_equal(g[i][s], q[i][s]), (i, s)
+            elif s > 0:
+                assert rel_l2(q[i][s], g[i][s]) < TOL[native.F32], (i, s)
+    i = 3                                      # the 48^3 instance: tiles wrap in x and y
+    hist = opr.parareal(oracle_F(cfgs[i]), oracle_G(cfgs[i]), u0s[i], cfgs[i].n_slices, 3)
+    for s in range(1, cfgs[i].n_slices + 1):
+        assert rel_l2(q[i][s], hist[3][s]) < TOL[native.F32], s
+
+
+def test_queue_autotune_and_stopping(monkeypatch):
+    cfgs, u0s = small_batch()
+    b = native.Batch(cfgs)
+    b.set_fine_mode(1)
+    b.autotune(None)
+    mode = b.fine_mode()
+    assert mode[0] == 1 and mode[1:] in [(64, 32, 1), (64, 16, 1), (32, 16, 1), (64, 32, 2)]
+    for i, u0 in enumerate(u0s):
+        b.set_problem(i, torch.from_numpy(u0).cuda())
+    b.serial_fine(as_reference=True)
+    k, d = b.iterate(4, 1e-5, native.STOP_DEFECT)
+    for i, cfg in enumerate(cfgs):
+        # the instance alone, with the launch shapes the batch's autotuner gave it
+        fine4, coarse4, serial4 = b.context(i).launch_shape()
+        for var, sh in (("PARAREAL_FINE_TILE", fine4), ("PARAREAL_COARSE_TILE", coarse4),
+                        ("PARAREAL_SERIAL_TILE", serial4)):
+            monkeypatch.setenv(var, ",".join(map(str, sh)))
+        solo = native.Parareal(cfg)
+        solo.set_problem(torch.from_numpy(u0s[i]).cuda())
+        solo.serial_fine(None, as_reference=True)
+        ks, hs = solo.iterate(4, 1e-5, native.STOP_DEFECT)
+        assert ks == k[i] and hs[-1, 2] == d[i], i
+        got = _all_slices(b.context(i), cfg)
+        want = _all_slices(solo, cfg)
+        for s in range(cfg.n_slices + 1):
+            assert np.array_equal(got[s], want[s]), (i, s)
+        solo.close()
+    b.close()
+
+
+def test_queue_mode_is_checked():
+    cfgs, _ = small_batch()
+    b = native.Batch(cfgs)
+    with pytest.raises(native.PararealError):
+        b.set_fine_mode(1, 16, 16, 1)           # not a compiled queue shape
+    b.close()
+    cfg64, _ = configs.small(n=16, n_slices=2, dtype=native.F64)
+    b = native.Batch([cfg64, cfg64])
+    with pytest.raises(native.PararealError):
+        b.set_fine_mode(1)                       # FP64 instances
+    b.close()
