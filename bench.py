@@ -282,6 +282,7 @@ def run(args):
                            else native.CORRECTION_STANDARD)
     cfg.coarse_transfer = (native.TRANSFER_SPECTRAL if args.transfer == "spectral"
                            else native.TRANSFER_BOX)
+    cfg.pipeline_blocks = args.pipeline
     n, N = cfg.n, cfg.n_slices
     P = n ** 3
     nf = round(cfg.T / N / cfg.dt_fine)
@@ -445,7 +446,7 @@ def run(args):
         "precision": "FP32 stencil; FP64 correction, norms and nu(t)",
         "data": "synthetic",
         "config": {"workload": desc, "correction_form": args.correction,
-                   "coarse_transfer": args.transfer,
+                   "coarse_transfer": args.transfer, "pipeline_blocks": args.pipeline,
                    "n": n, "n_slices": N, "fine_steps_per_slice": nf,
                    "l2": ("inputs larger than L2 (%.2f GB per field set)" % (4.0 * N * P / 1e9)),
                    "parallelism": "replicas" if world > 1 else "single GPU",
@@ -474,7 +475,7 @@ def run(args):
     del u0_dev
     torch.cuda.empty_cache()
     if rank == 0 and world == 1 and args.workload == "fp32_256" and not args.no_c4:
-        line["c4_learned_128"] = c4_learned_128(local)
+        line["c4_learned_128"] = c4_learned_128(local, pipeline=args.pipeline)
     if rank == 0 and world == 1 and args.workload == "fp32_256" and not args.no_c3:
         line["c3_batch64"] = {m: batch64(args.correction, m == "queue", 1, 1)
                               for m in ("graph", "queue")}
@@ -487,7 +488,7 @@ def run(args):
 
 # ------------------------------------------ the learned-propagator comparison
 
-def c4_learned_128(dev_index, steps=3, n_ics=63, epochs=10, batch=8, lr=1e-3):
+def c4_learned_128(dev_index, steps=3, n_ics=63, epochs=10, batch=8, lr=1e-3, pipeline=0):
     """The learned-coarse-propagator configuration at 128^3, N = 32: the linear
     learned propagator (stencil skip, nu as a factor), trained here on the
     pairs the fine solver generates (n_ics seeded k^-2 fields plus white noise,
@@ -506,7 +507,7 @@ def c4_learned_128(dev_index, steps=3, n_ics=63, epochs=10, batch=8, lr=1e-3):
         n, N, base.T, base.dt_fine, base.dt_coarse, base.coarse_factor, fine_dtype=native.F32,
         coarse_kind=kind, nu0=base.nu0, nu_amp=base.nu_amp, nu_omega=base.nu_omega,
         learned_skip=native.SKIP_STENCIL, learned_act=native.ACT_LINEAR,
-        correction_form=native.CORRECTION_DIFFERENCE, learned_eval=ev)
+        correction_form=native.CORRECTION_DIFFERENCE, learned_eval=ev, pipeline_blocks=pipeline)
     stream = torch.cuda.Stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -522,7 +523,7 @@ def c4_learned_128(dev_index, steps=3, n_ics=63, epochs=10, batch=8, lr=1e-3):
 
     out = {"workload": "learned_128: 128^3, N=32, dt_F=1/2048, stencil G = RK4 on 32^3 at 1/256; "
                        "linear learned G composed into one 9^3 kernel per slice",
-           "steps": steps}
+           "steps": steps, "pipeline_blocks": pipeline}
     with ClockSampler(dev_index) as clk:
         trainer = native.Parareal(mk(native.COARSE_LEARNED, native.EVAL_LAYERS), stream=stream)
         t0 = time.perf_counter()
@@ -976,13 +977,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pipeline", type=int, default=0,
+                    help="pipelined iterations: the next iteration's fine sweep in this many "
+                         "blocks on a second stream while the coarse chain runs (0: off)")
     ap.add_argument("--no-c3", action="store_true",
                     help="fp32_256: leave out the 64-instance batch comparison (graph and queue modes)")
     ap.add_argument("--no-c4", action="store_true",
                     help="skip the 128^3 learned-propagator comparison of the default line")
     ap.add_argument("--workload", default="fp32_256",
                     choices=["fp32_256", "fp32_128", "fp64_32", "learned_128", "learned_512",
-                             "learned_g", "batch64", "fine_sweep", "paper_faithful"])
+                             "learned_g", "batch64", "fine_sweep", "paper_faithful", "c4"])
     ap.add_argument("--slices", type=int, default=8)
     ap.add_argument("--correction", default="difference", choices=["difference", "standard"],
                     help="evaluation of the Parareal correction (fp32_256 / fp32_128 / batch64)")
@@ -1018,6 +1022,12 @@ def main():
         return run_learned_512(args)
     if args.workload == "batch64":
         return run_batch64(args)
+    if args.workload == "c4":
+        # the 128^3 learned-vs-stencil comparison of the headline line, alone
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps(c4_learned_128(0, pipeline=args.pipeline)))
+        return 0
     if args.workload == "fine_sweep":
         return run_fine_sweep(args)
     if args.workload == "paper_faithful":

@@ -120,7 +120,23 @@ typedef struct {
     int correction_form;   /* PARAREAL_CORRECTION_*: how Eq. (parareal) is evaluated */
     int learned_eval;      /* PARAREAL_EVAL_*: how a LINEAR learned propagator is evaluated */
     int coarse_transfer;   /* PARAREAL_TRANSFER_*: restriction / prolongation of a coarse-grid G */
+    int pipeline_blocks;   /* 0: off.  B > 0: pipelined iterations, see below */
 } parareal_config;
+
+/* Pipelined iterations (pipeline_blocks = B > 0; Sec. 2.2 notes that the
+ * fine propagations of the next iteration can start as soon as the serial
+ * coarse sweep has produced their initial values).  While an iteration's
+ * serial coarse sweep and corrections run on the context's stream, the next
+ * iteration's fine sweep F(U^{k+1}[n]) runs on a second stream of the
+ * context, in B blocks of consecutive slices, each launched as soon as the
+ * corrections have made its slices final; the next iteration's corrections
+ * wait only for the block they read.  F's results go to a second buffer, so
+ * the iterates are bit for bit those of pipeline_blocks = 0.  The fine sweep
+ * started for an iteration that the stopping rule then makes unnecessary is
+ * cancelled (its remaining launches exit at once); every call returns with
+ * the context's stream ordered after all of the context's work.  Needs the
+ * FP32 fused fine sweep (fine_dtype F32, fine_scheme C2) and N_p >= 2; costs
+ * a second (N_p+1) n^3 FP32 buffer.  Not for batch instances. */
 
 /* Transfers between the fine grid and the coarse grid of the stencil coarse
  * propagator (coarse_factor r > 1; Sec. 2.2.2 notes that a coarse propagator

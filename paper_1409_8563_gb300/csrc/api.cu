@@ -138,6 +138,12 @@ static parareal_status validate(const parareal_config *cfg, long long *Nf, long 
                            (cfg->fine_dtype == PARAREAL_F64 ? 8 : 4);
         if (mat > 160 * 1024) { *msg = "spectral transfer matrices larger than 160 KiB"; return PARAREAL_E_INVALID; }
     }
+    if (cfg->pipeline_blocks < 0) { *msg = "pipeline_blocks < 0"; return PARAREAL_E_INVALID; }
+    if (cfg->pipeline_blocks > 0 &&
+        (cfg->fine_dtype != PARAREAL_F32 || cfg->fine_scheme != PARAREAL_SCHEME_C2 || cfg->n_slices < 2)) {
+        *msg = "pipelined iterations need the FP32 fused fine sweep (F32, scheme C2) and n_slices >= 2";
+        return PARAREAL_E_INVALID;
+    }
     const double slice = cfg->T / cfg->n_slices;
     if (!is_integer_ratio(slice, cfg->dt_fine, Nf)) { *msg = "T/(n_slices dt_fine) must be an integer"; return PARAREAL_E_INVALID; }
     if (!is_integer_ratio(slice, cfg->dt_coarse, Nc)) { *msg = "T/(n_slices dt_coarse) must be an integer"; return PARAREAL_E_INVALID; }
@@ -232,7 +238,7 @@ static parareal_status prof_begin(parareal_ctx *c)
 template <typename T>
 parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, int first_slice, int count,
                           long long nsteps, double dt, int path, int tx, int ty, int zc, T *ws1,
-                          T *ws2, T *ws3, int slice_stride, int op)
+                          T *ws2, T *ws3, int slice_stride, int op, const int *cancel)
 {
     if (is_fused(path) && op != OP_C2)
         return fail(c, PARAREAL_E_INVALID, "the fused RK4 kernel implements the 7-point operator only");
@@ -250,6 +256,7 @@ parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, int first
     a.nu_amp = c->cfg.nu_amp;
     a.nu_omega = c->cfg.nu_omega;
     a.frozen = c->cfg.nu_mode == PARAREAL_NU_FROZEN;
+    a.cancel = cancel;
     if (is_fused(path)) {
         const T *src = in;
         const bool timed = c->prof && m == c->n;
@@ -289,10 +296,10 @@ parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, int first
 
 template parareal_status rk4_batch<float>(parareal_ctx *, int, const float *, float *, int, int,
                                           long long, double, int, int, int, int, float *, float *,
-                                          float *, int, int);
+                                          float *, int, int, const int *);
 template parareal_status rk4_batch<double>(parareal_ctx *, int, const double *, double *, int, int,
                                            long long, double, int, int, int, int, double *,
-                                           double *, double *, int, int);
+                                           double *, double *, int, int, const int *);
 
 template <typename T>
 parareal_status euler_batch(parareal_ctx *c, int m, const T *in, T *out, int first_slice,
@@ -339,12 +346,15 @@ template parareal_status euler_batch<double>(parareal_ctx *, int, const double *
 
 // ------------------------------------------------------------ propagators
 
-// Fv[s+1] = F(U[s]) for s in [first, first+count).
+// fvb[s+1] = F(U[s]) for s in [first, first+count) on c->st, in the given
+// launch shape.  conv (if set) is recorded once U has been read; cancel as in
+// StepArgs.
 template <typename T>
-static parareal_status fine_sweep_t(parareal_ctx *c, int first, int count)
+static parareal_status fine_sweep_range(parareal_ctx *c, int first, int count, void *fvb, int path,
+                                        int tx, int ty, int zc, cudaEvent_t conv, const int *cancel)
 {
     const long long P = c->P;
-    T *Fv = static_cast<T *>(c->Fv) + (long long)(first + 1) * P;
+    T *Fv = static_cast<T *>(fvb) + (long long)(first + 1) * P;
     const T *in;
     if (std::is_same<T, float>::value) {
         LK(launch_convert_f64_to_f32(c->U + (long long)first * P, reinterpret_cast<float *>(c->wC ? c->wC : c->wA),
@@ -353,11 +363,21 @@ static parareal_status fine_sweep_t(parareal_ctx *c, int first, int count)
     } else {
         in = reinterpret_cast<const T *>(c->U + (long long)first * P);
     }
+    if (conv) CK(cudaEventRecord(conv, c->st));
     // the fused path must not read and write the same buffer
     T *ws1 = static_cast<T *>(c->wA), *ws2 = static_cast<T *>(c->wB), *ws3 = static_cast<T *>(c->wC);
-    if (is_fused(c->fine_path) && in == ws1) std::swap(ws1, ws3);
-    return rk4_batch<T>(c, c->n, in, Fv, first, count, c->Nf, c->cfg.dt_fine, c->fine_path,
-                        c->fine_tx, c->fine_ty, c->fine_zc, ws1, ws2, ws3, 1, c->fine_op);
+    if (is_fused(path) && in == ws1) std::swap(ws1, ws3);
+    return rk4_batch<T>(c, c->n, in, Fv, first, count, c->Nf, c->cfg.dt_fine, path, tx, ty, zc, ws1,
+                        ws2, ws3, 1, c->fine_op, cancel);
+}
+
+// F(U^k[s]) into fv_of(k)[s+1] for s in [first, first+count), k = k_total.
+template <typename T>
+static parareal_status fine_sweep_t(parareal_ctx *c, int first, int count)
+{
+    c->spec_valid = false;
+    return fine_sweep_range<T>(c, first, count, fv_of(c, c->k_total), c->fine_path, c->fine_tx,
+                               c->fine_ty, c->fine_zc, nullptr, nullptr);
 }
 
 // The stencil coarse propagator of slice s on the fine grid, in FP64: RK4 on
@@ -480,7 +500,8 @@ template <typename T>
 static parareal_status correct_t(parareal_ctx *c, int s, const void *gnew, const void *gold,
                                  bool with_fine, double *dU = nullptr)
 {
-    const T *Fv = with_fine ? static_cast<const T *>(c->Fv) + (long long)(s + 1) * c->P : nullptr;
+    const T *Fv = with_fine ? static_cast<const T *>(fv_of(c, c->k_total)) + (long long)(s + 1) * c->P
+                            : nullptr;
     double *U = c->U + (long long)(s + 1) * c->P;
     if (!c->g_fine) {
         parareal_status ps = correct_coarse<T>(c, Fv, static_cast<const T *>(gnew),
@@ -513,6 +534,109 @@ static parareal_status coarse_chain(parareal_ctx *c, int first, int count, bool 
     return PARAREAL_OK;
 }
 
+// F(U^k[n]) of the open slices n = k_total..N-1 into fv_of(k_total), on c->st.
+parareal_status fine_sweep_open(parareal_ctx *c)
+{
+    return DISPATCH(c, fine_sweep_t, c->k_total, c->N - c->k_total);
+}
+
+parareal_status pipe_join(parareal_ctx *c)
+{
+    if (!c->st_f) return PARAREAL_OK;
+    CK(cudaEventRecord(c->ev_join, c->st_f));
+    CK(cudaStreamWaitEvent(c->st, c->ev_join, 0));
+    return PARAREAL_OK;
+}
+
+namespace {
+
+// The speculative sweep of one iteration (pipelined iterations): F(U^{k+1}[n])
+// for n in [K+1, N), in blocks launched on st_f as the chain finalises them.
+struct PipeSpec {
+    parareal_ctx *c;
+    int p = 0;                 // parity of K+1: the buffers and events it fills
+    int nb = 0;                // number of blocks (0: nothing to speculate)
+    int next = 0;              // next block to launch
+
+    PipeSpec(parareal_ctx *cc, int K) : c(cc)
+    {
+        const int cnt = c->N - (K + 1);
+        if (!c->Fv2 || cnt <= 0) return;
+        nb = std::min(c->cfg.pipeline_blocks, cnt);
+        p = (K + 1) & 1;
+        c->spec_lo[p].assign(nb, 0);
+        c->spec_hi[p].assign(nb, 0);
+        for (int j = 0; j < nb; ++j) {
+            c->spec_lo[p][j] = K + 1 + (int)((long long)j * cnt / nb);
+            c->spec_hi[p][j] = K + 1 + (int)((long long)(j + 1) * cnt / nb);
+        }
+    }
+
+    // After the correction that made U[m] final: launch every block whose
+    // last slice is m.
+    parareal_status after_final(int m)
+    {
+        while (next < nb && c->spec_hi[p][next] - 1 == m) {
+            parareal_status s = launch(next);
+            if (s != PARAREAL_OK) return s;
+            ++next;
+        }
+        return PARAREAL_OK;
+    }
+
+    parareal_status launch(int j)
+    {
+        CK(cudaEventRecord(c->ev_fork, c->st));
+        CK(cudaStreamWaitEvent(c->st_f, c->ev_fork, 0));
+        if (j == 0) CK(cudaMemsetAsync(c->cancel, 0, sizeof(int), c->st_f));
+        const int lo = c->spec_lo[p][j], hi = c->spec_hi[p][j];
+        const cudaStream_t main_st = c->st;
+        c->st = c->st_f;
+        parareal_status s = fine_sweep_range<float>(c, lo, hi - lo, fv_of(c, p), c->pipe_path,
+                                                    c->pipe_tx, c->pipe_ty, c->pipe_zc,
+                                                    c->ev_conv[p][j], c->cancel);
+        c->st = main_st;
+        if (s != PARAREAL_OK) return s;
+        CK(cudaEventRecord(c->ev_done[p][j], c->st_f));
+        return PARAREAL_OK;
+    }
+};
+
+// Waits of an iteration's chain on the speculative sweep that produced its
+// Fv (host loop, events recorded by the previous enqueue).
+struct PipeWait {
+    parareal_ctx *c;
+    int p = 0, nb = 0;
+    int done_upto = -1, conv_upto = -1;   // blocks already waited on
+
+    PipeWait(parareal_ctx *cc, int K, bool active) : c(cc)
+    {
+        if (!active) return;
+        p = K & 1;
+        nb = (int)c->spec_lo[p].size();
+    }
+
+    int block_of(int s) const
+    {
+        for (int j = 0; j < nb; ++j)
+            if (s >= c->spec_lo[p][j] && s < c->spec_hi[p][j]) return j;
+        return -1;
+    }
+
+    // Before the correction of chain step n (reads Fv[n+1] = F(U[n]), writes U[n+1]).
+    parareal_status before_step(int n)
+    {
+        if (nb == 0) return PARAREAL_OK;
+        const int jd = block_of(n);
+        for (; jd >= 0 && done_upto < jd; ++done_upto) CK(cudaStreamWaitEvent(c->st, c->ev_done[p][done_upto + 1], 0));
+        const int jc = block_of(n + 1);
+        for (; jc >= 0 && conv_upto < jc; ++conv_upto) CK(cudaStreamWaitEvent(c->st, c->ev_conv[p][conv_upto + 1], 0));
+        return PARAREAL_OK;
+    }
+};
+
+}  // namespace
+
 // Device work of one Parareal iteration (Algorithm 1 loop body for every
 // open slice), enqueued on c->st without any host synchronisation:
 // fine sweep of slices K..N-1, then the serial coarse sweep with the
@@ -520,43 +644,76 @@ static parareal_status coarse_chain(parareal_ctx *c, int first, int count, bool 
 // into slot N+1 of slice_norms.  K = c->k_total: U[0..K] are already exact.
 // with_fine = false leaves out the fine sweep (the caller has put F(U^k[n])
 // into Fv[n+1] another way); copy_norms = false leaves the norms on the device.
-parareal_status iter_enqueue(parareal_ctx *c, bool copy_norms, bool with_fine)
+//
+// Pipelined iterations: the fine sweep of this iteration was started by the
+// previous one (or runs here when it was not), and this iteration starts the
+// next one's, F(U^{k+1}[n]) into fv_of(K+1), block by block on st_f right
+// after the correction that makes a block's last slice final.  The chain
+// waits for a block of the previous speculation before it reads the block's
+// F values and before it overwrites the U values the block reads.
+parareal_status iter_enqueue(parareal_ctx *c, bool copy_norms, bool with_fine, bool capture,
+                             void (*stop_eval)(parareal_ctx *, void *), void *stop_arg)
 {
     const int K = c->k_total;
+    const bool pipe = c->Fv2 != nullptr;
     parareal_status s = PARAREAL_OK;
-    if (with_fine) {
-        s = DISPATCH(c, fine_sweep_t, K, c->N - K);
+    // a graph body assumes the speculative Fv of its iteration (the host
+    // provides it before the first body)
+    const bool have_fv = pipe && (capture || c->spec_valid);
+    if (with_fine && !have_fv) {
+        s = fine_sweep_open(c);
         if (s != PARAREAL_OK) return s;
     }
+    PipeWait wait(c, K, pipe && !capture && c->spec_valid && c->spec_events);
+    PipeSpec spec(c, K);
+    auto step_done = [&](int n) -> parareal_status {     // U[n+1] is final
+        return spec.after_final(n + 1);
+    };
     if (c->cfg.correction_form == PARAREAL_CORRECTION_DIFFERENCE) {
         // U[n+1] = Fv[n+1] + G(D_n), D_n = U^{k+1}[n] - U^k[n] (G linear); the
         // correction of slice n writes D_{n+1}.  D_K = 0: slice K+1 takes Fv alone.
         double *Din = c->dA, *Dout = c->dB;
+        if ((s = wait.before_step(K)) != PARAREAL_OK) return s;
         s = DISPATCH(c, correct_t, K, g_cur(c, K + 1), g_cur(c, K + 1), true, Din);
         if (s != PARAREAL_OK) return s;
+        if ((s = step_done(K)) != PARAREAL_OK) return s;
         for (int n = K + 1; n < c->N; ++n) {
             s = DISPATCH(c, coarse_apply_t, Din, n, c->gspare);
             if (s != PARAREAL_OK) return s;
+            if ((s = wait.before_step(n)) != PARAREAL_OK) return s;
             s = DISPATCH(c, correct_t, n, c->gspare, nullptr, true, Dout);
             if (s != PARAREAL_OK) return s;
+            if ((s = step_done(n)) != PARAREAL_OK) return s;
             std::swap(Din, Dout);
         }
     } else {
         // slice K+1: its input U[K] did not change, so G's difference is zero
+        if ((s = wait.before_step(K)) != PARAREAL_OK) return s;
         s = DISPATCH(c, correct_t, K, g_cur(c, K + 1), g_cur(c, K + 1), true);
         if (s != PARAREAL_OK) return s;
+        if ((s = step_done(K)) != PARAREAL_OK) return s;
         for (int n = K + 1; n < c->N; ++n) {
             void *g = g_next(c, n + 1);
             s = DISPATCH(c, coarse_apply_t, c->U + (long long)n * c->P, n, g);
             if (s != PARAREAL_OK) return s;
+            if ((s = wait.before_step(n)) != PARAREAL_OK) return s;
             s = DISPATCH(c, correct_t, n, g, g_cur(c, n + 1), true);
             if (s != PARAREAL_OK) return s;
+            if ((s = step_done(n)) != PARAREAL_OK) return s;
             c->gcur[n + 1] ^= 1;
         }
     }
     if (c->has_ref) {
         LK(launch_diff_norms<double>(c->U + (long long)c->N * c->P, c->ref, c->P, c->partials, c->nblk, c->st));
         LK(launch_reduce_partials(c->partials, c->nblk, c->slice_norms + 5ll * (c->N + 1), c->st));
+    }
+    c->spec_pending = spec.nb > 0;
+    if (pipe && capture && spec.nb > 0) {
+        // inside a graph body: decide on the device whether the speculative
+        // sweep is still needed, then join its branch
+        if (stop_eval) stop_eval(c, stop_arg);
+        s = pipe_join(c);
+        if (s != PARAREAL_OK) return s;
     }
     if (copy_norms)
         CK(cudaMemcpyAsync(c->h_norms, c->slice_norms, sizeof(double) * 5 * (c->N + 2),
@@ -659,6 +816,8 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
         delete c;
         return fail(nullptr, PARAREAL_E_INVALID, "unsupported launch shape override");
     }
+    // pipelined: no cooperative persistent launch beside the side stream's sweep
+    if (cfg->pipeline_blocks > 0 && c->coarse_path == PATH_PERSIST) c->coarse_path = PATH_STAGED;
     c->fine_op = cfg->fine_scheme == PARAREAL_SCHEME_C4 ? OP_C4 : OP_C2;
     if (c->fine_op != OP_C2) {
         // the fused kernels implement the 7-point operator only
@@ -680,6 +839,34 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
     bool ok = cudaGetDevice(&c->dev) == cudaSuccess;
     ok = ok && alloc((void **)&c->U, (N + 1) * P * sizeof(double));
     ok = ok && alloc(&c->Fv, (N + 1) * P * e);
+    if (cfg->pipeline_blocks > 0) {
+        // the second F buffer, the side stream (lowest priority: the serial
+        // chain on the context's stream goes first), the cancel flag, events
+        int lo = 0, hi = 0;
+        ok = ok && alloc(&c->Fv2, (N + 1) * P * e) && alloc((void **)&c->cancel, sizeof(int)) &&
+             cudaMemset(c->cancel, 0, sizeof(int)) == cudaSuccess &&
+             cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
+             cudaStreamCreateWithPriority(&c->st_f, cudaStreamNonBlocking, lo) == cudaSuccess &&
+             cudaStreamCreateWithPriority(&c->st_hi, cudaStreamNonBlocking, hi) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) == cudaSuccess;
+        const int nb = std::min(cfg->pipeline_blocks, c->N - 1);
+        for (int p = 0; p < 2 && ok; ++p) {
+            c->ev_conv[p].assign(nb, nullptr);
+            c->ev_done[p].assign(nb, nullptr);
+            for (int j = 0; j < nb && ok; ++j)
+                ok = cudaEventCreateWithFlags(&c->ev_conv[p][j], cudaEventDisableTiming) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&c->ev_done[p][j], cudaEventDisableTiming) == cudaSuccess;
+        }
+        // launch shape of a block: the fused shape for its slice count
+        default_tiles(PARAREAL_F32, c->n, (c->N - 1 + nb - 1) / nb, &c->pipe_path, &c->pipe_tx,
+                      &c->pipe_ty, &c->pipe_zc);
+        if (!is_fused(c->pipe_path)) { c->pipe_path = c->fine_path; c->pipe_tx = c->fine_tx; c->pipe_ty = c->fine_ty; c->pipe_zc = c->fine_zc; }
+        ok = ok && tile_override("PARAREAL_PIPE_TILE", PARAREAL_F32, c->n, &c->pipe_path, &c->pipe_tx,
+                                 &c->pipe_ty, &c->pipe_zc) && is_fused(c->pipe_path);
+    }
     c->gold.assign(N + 1, nullptr);
     c->gold2.assign(N + 1, nullptr);
     c->gcur.assign(N + 1, 0);
@@ -743,7 +930,9 @@ extern "C" void parareal_destroy(parareal_ctx *c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->st);
-    void *ptrs[] = {c->U, c->Fv, c->gspare, c->wA, c->wB, c->wC, c->cA, c->cB, c->cC, c->cD,
+    if (c->st_f) cudaStreamSynchronize(c->st_f);
+    if (c->st_hi) cudaStreamSynchronize(c->st_hi);
+    void *ptrs[] = {c->U, c->Fv, c->Fv2, c->cancel, c->gspare, c->wA, c->wB, c->wC, c->cA, c->cB, c->cC, c->cD,
                     c->tmpd, c->wS, c->ref, c->partials, c->slice_norms, c->dA, c->dB,
                     c->sp_R, c->sp_Rt, c->sp_P, c->sp_Pt, c->sp_work, c->sp_fine, c->bar};
     for (void *p : ptrs)
@@ -754,7 +943,17 @@ extern "C" void parareal_destroy(parareal_ctx *c)
         if (p) cudaFree(p);
     if (c->h_norms) cudaFreeHost(c->h_norms);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (int p = 0; p < 2; ++p) {
+        for (cudaEvent_t e : c->ev_conv[p]) if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : c->ev_done[p]) if (e) cudaEventDestroy(e);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
     solve_graph_free(c);
+    if (c->st_f) cudaStreamDestroy(c->st_f);
+    if (c->st_hi) cudaStreamDestroy(c->st_hi);
     net_free(c);
     delete c;
 }
@@ -836,6 +1035,7 @@ static parareal_status store_field(parareal_ctx *c, void *dst, const double *src
 extern "C" parareal_status parareal_set_problem(parareal_ctx *c, const void *u0, int dtype, int mem)
 {
     if (!c) return PARAREAL_E_INVALID;
+    c->spec_valid = false;      // U, F or the sweep workspaces change
     parareal_status s = load_field(c, c->U, u0, dtype, mem);
     if (s != PARAREAL_OK) return s;
     c->has_problem = true;
@@ -869,6 +1069,7 @@ extern "C" parareal_status parareal_get_slice(parareal_ctx *c, int slice, void *
 extern "C" parareal_status parareal_set_slice(parareal_ctx *c, int slice, const void *src, int dtype, int mem)
 {
     if (!c) return PARAREAL_E_INVALID;
+    c->spec_valid = false;      // U, F or the sweep workspaces change
     if (slice < 0 || slice > c->N) return fail(c, PARAREAL_E_INVALID, "slice out of range");
     return load_field(c, c->U + (long long)slice * c->P, src, dtype, mem);
 }
@@ -1014,6 +1215,7 @@ extern "C" parareal_status parareal_save_state(parareal_ctx *c, void *host, size
 extern "C" parareal_status parareal_load_state(parareal_ctx *c, const void *host, size_t bytes)
 {
     if (!c) return PARAREAL_E_INVALID;
+    c->spec_valid = false;      // U, F or the sweep workspaces change
     if (!host || bytes < sizeof(StateHeader)) return fail(c, PARAREAL_E_INVALID, "state buffer too small");
     StateHeader h;
     std::memcpy(&h, host, sizeof h);
@@ -1061,6 +1263,7 @@ extern "C" parareal_status parareal_fine_sweep(parareal_ctx *c, int first, int c
 extern "C" parareal_status parareal_coarse_sweep(parareal_ctx *c, int first, int count, int chain)
 {
     if (!c) return PARAREAL_E_INVALID;
+    c->spec_valid = false;      // U, F or the sweep workspaces change
     if (first < 0 || count < 0 || first + count > c->N) return fail(c, PARAREAL_E_INVALID, "slice range");
     return coarse_chain(c, first, count, chain != 0);
 }
@@ -1074,6 +1277,7 @@ extern "C" parareal_status parareal_iterate(parareal_ctx *c, int k_max, double t
     if (k_max < 0) return fail(c, PARAREAL_E_INVALID, "k_max < 0");
     if (stop_rule == PARAREAL_STOP_DEFECT && !c->has_ref) return fail(c, PARAREAL_E_STATE, "no reference set");
     if (stop_rule < 0 || stop_rule > 2) return fail(c, PARAREAL_E_INVALID, "stop_rule");
+    ChainStream chain_stream(c);
     parareal_status s;
     if (!c->started) {
         std::fill(c->gcur.begin(), c->gcur.end(), 0);
@@ -1083,15 +1287,27 @@ extern "C" parareal_status parareal_iterate(parareal_ctx *c, int k_max, double t
     }
     const auto t0 = std::chrono::steady_clock::now();
     int done = 0;
+    bool stopped = false;
     for (; done < k_max && c->k_total < c->N; ++done) {
         s = iter_enqueue(c);
-        if (s != PARAREAL_OK) return s;
-        CK(cudaStreamSynchronize(c->st));
-        s = device_check(c);
-        if (s != PARAREAL_OK) return s;
-        double dmax, l2max, d;
-        s = iter_finish(c, &dmax, &l2max, &d);
-        if (s != PARAREAL_OK) return s;
+        if (s == PARAREAL_OK) {
+            c->spec_valid = false;
+            if (cudaStreamSynchronize(c->st) != cudaSuccess) s = fail(c, PARAREAL_E_CUDA, "iteration failed");
+        }
+        if (s == PARAREAL_OK) s = device_check(c);
+        double dmax = 0.0, l2max = 0.0, d = -1.0;
+        if (s == PARAREAL_OK) s = iter_finish(c, &dmax, &l2max, &d);
+        if (s != PARAREAL_OK) {
+            // a failed iteration leaves no usable speculative sweep
+            if (c->st_f) {
+                cudaMemsetAsync(c->cancel, 1, sizeof(int), c->st);
+                pipe_join(c);
+            }
+            return s;
+        }
+        // the next iteration's F, if this one started it (pipelined)
+        c->spec_valid = c->spec_pending;
+        c->spec_events = c->spec_pending;
         if (hist) {
             hist[4 * done + 0] = dmax;
             hist[4 * done + 1] = l2max;
@@ -1099,8 +1315,21 @@ extern "C" parareal_status parareal_iterate(parareal_ctx *c, int k_max, double t
             hist[4 * done + 3] =
                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         }
-        if (stop_rule == PARAREAL_STOP_DIFF && dmax <= tol) { ++done; break; }
-        if (stop_rule == PARAREAL_STOP_DEFECT && d <= tol) { ++done; break; }
+        if ((stop_rule == PARAREAL_STOP_DIFF && dmax <= tol) ||
+            (stop_rule == PARAREAL_STOP_DEFECT && d <= tol)) {
+            ++done;
+            stopped = true;
+            break;
+        }
+    }
+    if (c->st_f) {
+        if (stopped && c->spec_valid) {
+            // the speculative sweep is not needed: its remaining launches exit
+            CK(cudaMemsetAsync(c->cancel, 1, sizeof(int), c->st));
+            c->spec_valid = false;
+        }
+        s = pipe_join(c);
+        if (s != PARAREAL_OK) return s;
     }
     if (k_done) *k_done = done;
     return PARAREAL_OK;
@@ -1149,6 +1378,7 @@ extern "C" parareal_status parareal_serial_fine(parareal_ctx *c, void *dst, int 
                                                 int as_reference)
 {
     if (!c) return PARAREAL_E_INVALID;
+    c->spec_valid = false;      // U, F or the sweep workspaces change
     if (!c->has_problem) return fail(c, PARAREAL_E_STATE, "set_problem first");
     // march slice after slice in the fine arithmetic type; slice boundaries
     // pass through Fv[1] (F's output of one slice is the next slice's input)
@@ -1271,6 +1501,7 @@ extern "C" parareal_status parareal_propagate(parareal_ctx *c, int which, const 
                                               void *dst, int dtype, int first, int count)
 {
     if (!c) return PARAREAL_E_INVALID;
+    c->spec_valid = false;      // U, F or the sweep workspaces change
     if (!src || !dst || (which != 0 && which != 1)) return fail(c, PARAREAL_E_INVALID, "arguments");
     if (dtype != PARAREAL_F32 && dtype != PARAREAL_F64) return fail(c, PARAREAL_E_INVALID, "dtype");
     if (first < 0 || count < 0 || first + count > c->N) return fail(c, PARAREAL_E_INVALID, "slice range");
@@ -1312,7 +1543,9 @@ static parareal_status time_shape(parareal_ctx *c, int m, int count, int path, i
 
 // Candidates: every compiled fused shape (one and two rows per thread) that
 // divides m, whole-column and chunked z marches, and the per-stage path.
-static void candidates(int dtype, int m, std::vector<std::array<int, 4>> *out)
+enum { NO_STAGED = 1, NO_PERSIST = 2 };
+
+static void candidates(int dtype, int m, std::vector<std::array<int, 4>> *out, int exclude = 0)
 {
     const int shapes[][2] = {{64, 32}, {64, 16}, {64, 8}, {32, 32}, {32, 16}, {32, 8}, {16, 16}, {16, 8}};
     for (int path : {PATH_FUSED, PATH_FUSED2})
@@ -1323,17 +1556,18 @@ static void candidates(int dtype, int m, std::vector<std::array<int, 4>> *out)
                 if (zc <= m / 8) break;
             }
         }
-    out->push_back({PATH_STAGED, 16, 8, m});
-    out->push_back({PATH_PERSIST, 16, 8, m});
+    if (!(exclude & NO_STAGED)) out->push_back({PATH_STAGED, 16, 8, m});
+    if (!(exclude & NO_PERSIST)) out->push_back({PATH_PERSIST, 16, 8, m});
 }
 
-static std::string tune_key(int dtype, int m, int count)
+static std::string tune_key(int dtype, int m, int count, int exclude)
 {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    char k[96];
-    std::snprintf(k, sizeof k, "n=%d dtype=%d count=%d sms=%d", m, dtype, count, sms);
+    char k[128];
+    std::snprintf(k, sizeof k, "n=%d dtype=%d count=%d sms=%d%s%s", m, dtype, count, sms,
+                  (exclude & NO_STAGED) ? " nostaged" : "", (exclude & NO_PERSIST) ? " nopersist" : "");
     return k;
 }
 
@@ -1368,20 +1602,21 @@ static void cache_store(const char *path, const std::string &key, const int *sh,
 
 template <typename T>
 static parareal_status tune_one(parareal_ctx *c, const char *cache, int m, int count, double dt,
-                                int *path, int *tx, int *ty, int *zc, double *best_ms)
+                                int *path, int *tx, int *ty, int *zc, double *best_ms, int exclude = 0)
 {
     const int dtype = c->f64 ? PARAREAL_F64 : PARAREAL_F32;
-    const std::string key = tune_key(dtype, m, count);
+    const std::string key = tune_key(dtype, m, count, exclude);
     int sh[4];
     if (cache_lookup(cache, key, sh) &&
-        (sh[0] == PATH_STAGED || sh[0] == PATH_PERSIST ||
+        ((sh[0] == PATH_STAGED && !(exclude & NO_STAGED)) ||
+         (sh[0] == PATH_PERSIST && !(exclude & NO_PERSIST)) ||
          (is_fused(sh[0]) && rk4_fused_supported(dtype, m, sh[1], sh[2], fused_rows(sh[0]))))) {
         *path = sh[0]; *tx = sh[1]; *ty = sh[2]; *zc = sh[3];
         *best_ms = -1.0;
         return PARAREAL_OK;
     }
     std::vector<std::array<int, 4>> cand;
-    candidates(dtype, m, &cand);
+    candidates(dtype, m, &cand, exclude);
     double best = 1e30;
     std::array<int, 4> pick = cand.back();
     for (auto &k : cand) {
@@ -1400,6 +1635,7 @@ static parareal_status tune_one(parareal_ctx *c, const char *cache, int m, int c
 extern "C" parareal_status parareal_autotune(parareal_ctx *c, const char *cache_path, double *ms2)
 {
     if (!c) return PARAREAL_E_INVALID;
+    c->spec_valid = false;      // U, F or the sweep workspaces change
     CK(cudaMemsetAsync(c->wC, 0, (size_t)c->N * c->P * c->esz, c->st));
     CK(cudaMemsetAsync(c->cA, 0, (size_t)(c->r > 1 ? c->Pc : c->P) * c->esz, c->st));
     double fms = 0.0, cms = 0.0;
@@ -1430,15 +1666,27 @@ extern "C" parareal_status parareal_autotune(parareal_ctx *c, const char *cache_
     if ((c->cfg.coarse_kind == PARAREAL_COARSE_STENCIL ||
          c->cfg.learned_skip == PARAREAL_SKIP_STENCIL) && c->nc >= 8) {
         // the coarse sweep runs one field at a time on the coarse grid
+        // (pipelined: no cooperative persistent launch beside the side stream's sweep)
+        const int ex = c->Fv2 ? NO_PERSIST : 0;
         void *saveC = c->wC;
         c->wC = c->cA;   // input of the timed coarse steps
         if (c->f64)
             s = tune_one<double>(c, cache_path, c->nc, 1, c->cfg.dt_coarse, &c->coarse_path,
-                                 &c->coarse_tx, &c->coarse_ty, &c->coarse_zc, &cms);
+                                 &c->coarse_tx, &c->coarse_ty, &c->coarse_zc, &cms, ex);
         else
             s = tune_one<float>(c, cache_path, c->nc, 1, c->cfg.dt_coarse, &c->coarse_path,
-                                &c->coarse_tx, &c->coarse_ty, &c->coarse_zc, &cms);
+                                &c->coarse_tx, &c->coarse_ty, &c->coarse_zc, &cms, ex);
         c->wC = saveC;
+        if (s != PARAREAL_OK) return s;
+    }
+    const char *pipe_env = std::getenv("PARAREAL_PIPE_TILE");
+    if (c->Fv2 && !(pipe_env && *pipe_env)) {
+        // the speculative sweep's blocks: fused shapes only (they honour the cancel flag)
+        const int nb = (int)c->ev_done[0].size();
+        double pms = 0.0;
+        s = tune_one<float>(c, cache_path, c->n, (c->N - 1 + nb - 1) / nb, c->cfg.dt_fine,
+                            &c->pipe_path, &c->pipe_tx, &c->pipe_ty, &c->pipe_zc, &pms,
+                            NO_STAGED | NO_PERSIST);
         if (s != PARAREAL_OK) return s;
     }
     if (ms2) { ms2[0] = fms; ms2[1] = cms; }

@@ -67,6 +67,9 @@ extern "C" parareal_status parareal_batch_create(const parareal_config *cfgs, in
 {
     if (!out || !cfgs || count < 1) return PARAREAL_E_INVALID;
     *out = nullptr;
+    // the round graph overlaps instances already; pipelined instances are not supported
+    for (int i = 0; i < count; ++i)
+        if (cfgs[i].pipeline_blocks != 0) return PARAREAL_E_INVALID;
     parareal_batch *b = new parareal_batch();
     b->main = static_cast<cudaStream_t>(stream);
     if (!b->main) {

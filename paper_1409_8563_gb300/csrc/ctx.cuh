@@ -62,6 +62,23 @@ struct parareal_ctx {
 
     double *U = nullptr;
     void *Fv = nullptr;
+    // pipelined iterations (cfg.pipeline_blocks > 0): F(U^k[n]) of iteration
+    // k lives in Fv for even k and in Fv2 for odd k; the next iteration's
+    // sweep runs on st_f, block by block, while the serial chain corrects
+    void *Fv2 = nullptr;
+    cudaStream_t st_f = nullptr;
+    int *cancel = nullptr;            // device flag read by the speculative sweep's launches
+    bool spec_valid = false;          // fv_of(k_total) holds F(U^k[n]) for the open slices
+    bool spec_events = false;         // ... with the block events of a host-loop enqueue
+    bool spec_pending = false;        // the last enqueue started the next iteration's sweep
+    std::vector<int> spec_lo[2], spec_hi[2];           // block slice ranges, by parity of k
+    std::vector<cudaEvent_t> ev_conv[2], ev_done[2];   // per block: input read / sweep done
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the serial chain of pipelined iterations runs on st_hi (highest
+    // priority), ordered after / before the caller's stream by ev_in / ev_out
+    cudaStream_t st_hi = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int pipe_path = PATH_FUSED, pipe_tx = 64, pipe_ty = 16, pipe_zc = 0;   // block launch shape
     // G(U^k[s-1]) for s = 1..N (index 0 unused) lives in gold[s] or gold2[s]:
     // gcur[s] names the current one, the other receives the next G output.
     // The roles follow from the iteration count alone (no pointer swaps), so
@@ -114,6 +131,9 @@ struct parareal_ctx {
 
 parareal_status fail(parareal_ctx *c, parareal_status s, const std::string &msg);
 
+// The buffer of F(U^k[n]) for iteration k.
+inline void *fv_of(const parareal_ctx *c, int k) { return (c->Fv2 && (k & 1)) ? c->Fv2 : c->Fv; }
+
 // The current and the next buffer of the stored G output of slice s.
 inline void *g_cur(parareal_ctx *c, int s) { return c->gcur[s] ? c->gold2[s] : c->gold[s]; }
 inline void *g_next(parareal_ctx *c, int s) { return c->gcur[s] ? c->gold[s] : c->gold2[s]; }
@@ -134,7 +154,8 @@ inline void *g_next(parareal_ctx *c, int s) { return c->gcur[s] ? c->gold[s] : c
 template <typename T>
 parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, int first_slice, int count,
                           long long nsteps, double dt, int path, int tx, int ty, int zc, T *ws1,
-                          T *ws2, T *ws3, int slice_stride = 1, int op = pr::OP_C2);
+                          T *ws2, T *ws3, int slice_stride = 1, int op = pr::OP_C2,
+                          const int *cancel = nullptr);
 
 // api.cu: nsteps forward Euler steps (Algorithm 2) of `count` fields with
 // operator op; in may equal out; ws1/ws2 are count*m^3 workspaces.
@@ -142,8 +163,48 @@ template <typename T>
 parareal_status euler_batch(parareal_ctx *c, int m, const T *in, T *out, int first_slice,
                             int count, long long nsteps, double dt, int op, T *ws1, T *ws2);
 
-// api.cu: one Parareal iteration split into device work and host bookkeeping
-parareal_status iter_enqueue(parareal_ctx *c, bool copy_norms = true, bool with_fine = true);
+// api.cu: one Parareal iteration split into device work and host bookkeeping.
+// With pipelining, `capture` marks an enqueue inside a graph capture: the
+// side branch is joined before return, no event of an earlier enqueue is
+// waited on, and `stop_eval` (if set) is enqueued on the main branch after
+// the norms and before the join (it sets the cancel flag).
+parareal_status iter_enqueue(parareal_ctx *c, bool copy_norms = true, bool with_fine = true,
+                             bool capture = false, void (*stop_eval)(parareal_ctx *, void *) = nullptr,
+                             void *stop_arg = nullptr);
+// api.cu: order the context's stream after the pipelined side stream
+parareal_status pipe_join(parareal_ctx *c);
+
+// Pipelined iterations run their serial chain on the context's high-priority
+// stream, so that the chain's small kernels take SMs ahead of the queued CTAs
+// of the speculative sweep: for the lifetime of this guard c->st is that
+// stream, ordered after the caller's stream on entry; on exit the caller's
+// stream is ordered after it.
+struct ChainStream {
+    parareal_ctx *c;
+    cudaStream_t user = nullptr;
+    bool on = false;
+    explicit ChainStream(parareal_ctx *cc) : c(cc)
+    {
+        if (!c->st_hi || c->st == c->st_hi) return;
+        user = c->st;
+        if (cudaEventRecord(c->ev_in, user) != cudaSuccess ||
+            cudaStreamWaitEvent(c->st_hi, c->ev_in, 0) != cudaSuccess)
+            return;
+        c->st = c->st_hi;
+        on = true;
+    }
+    ~ChainStream()
+    {
+        if (!on) return;
+        cudaEventRecord(c->ev_out, c->st_hi);
+        cudaStreamWaitEvent(user, c->ev_out, 0);
+        c->st = user;
+    }
+    ChainStream(const ChainStream &) = delete;
+    ChainStream &operator=(const ChainStream &) = delete;
+};
+// api.cu: F(U^k[n]) of the open slices into fv_of(k) on the context's stream
+parareal_status fine_sweep_open(parareal_ctx *c);
 parareal_status iter_finish(parareal_ctx *c, double *dmax, double *l2max, double *d);
 
 // api.cu: the stencil coarse propagator of slice s, prolonged to the fine

@@ -29,6 +29,8 @@ struct StepArgs {
     double nu0, nu_amp, nu_omega;
     int frozen;               // nu at step start for all stages
     int op;                   // OP_*: spatial operator (the fused kernel is OP_C2 only)
+    const int *cancel;        // fused kernel: non-null and nonzero at a CTA's start -> the
+                              // CTA returns at once (a speculative sweep no longer needed)
 };
 
 // Spatial operators.  OP_C2: 7-point Laplacian, centred first differences.

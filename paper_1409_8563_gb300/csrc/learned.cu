@@ -285,6 +285,7 @@ extern "C" parareal_status parareal_coarse_model_grad(parareal_ctx *c, const flo
                                                       const float *target, const int *slices,
                                                       int count, float *grad_out, double *loss)
 {
+    if (c) c->spec_valid = false;      // U, F or the sweep workspaces may change
     parareal_status s = need_learned(c);
     if (s != PARAREAL_OK) return s;
     if (!u || !target || !slices || count < 1 || !grad_out) return fail(c, PARAREAL_E_INVALID, "arguments");
@@ -320,6 +321,7 @@ extern "C" parareal_status parareal_train_coarse(parareal_ctx *c, const float *p
                                                  int n_pairs, const parareal_train_config *tc,
                                                  double *loss_hist)
 {
+    if (c) c->spec_valid = false;      // U, F or the sweep workspaces may change
     parareal_status s = need_learned(c);
     if (s != PARAREAL_OK) return s;
     if (!pairs_u || !pairs_f || !pair_slice || !tc || n_pairs < 1 || tc->epochs < 0 || tc->batch < 1)
@@ -451,6 +453,7 @@ static parareal_status make_pairs_t(parareal_ctx *c, const float *ics, int n_ics
 extern "C" parareal_status parareal_make_pairs(parareal_ctx *c, const float *ics, int n_ics,
                                                float *pairs_u, float *pairs_f, int *pair_slice)
 {
+    if (c) c->spec_valid = false;      // U, F or the sweep workspaces may change
     parareal_status s = need_learned(c);
     if (s != PARAREAL_OK) return s;
     if (!ics || n_ics < 1 || !pairs_u || !pairs_f) return fail(c, PARAREAL_E_INVALID, "arguments");

@@ -34,6 +34,8 @@ struct DevSolve {
     int done, status;               // iterations run; 1 = non-finite value seen
     double tol;
     unsigned long long t0;          // %globaltimer at the start, ns
+    int cancelled;                  // pipelined: the last speculative sweep was cancelled
+    int pad;
 };
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -51,6 +53,50 @@ __global__ void solve_pre_kernel(DevSolve *d, cudaGraphConditionalHandle which)
     cudaGraphSetConditional(which, (unsigned)(d->K0 + d->done));
 }
 
+// The norms of the iteration with K = K0 + done exact slices: the largest
+// relative changes of slices K+1..N, the defect (or -1), non-finite values.
+__device__ void iteration_norms(const DevSolve *d, const double *__restrict__ norms, int has_ref,
+                                double *dmax, double *l2max, double *defect, int *bad)
+{
+    const int N = d->N, K = d->K0 + d->done;
+    *dmax = 0.0;
+    *l2max = 0.0;
+    *defect = -1.0;
+    *bad = 0;
+    for (int s = K + 1; s <= N; ++s) {
+        const double *q = norms + 5 * s;
+        *bad |= q[4] != 0.0;
+        const double di = q[1] > 0.0 ? q[0] / q[1] : q[0];
+        const double dl = q[3] > 0.0 ? sqrt(q[2] / q[3]) : sqrt(q[2]);
+        *dmax = di > *dmax ? di : *dmax;
+        *l2max = dl > *l2max ? dl : *l2max;
+    }
+    if (has_ref) {
+        const double *q = norms + 5 * (N + 1);
+        *bad |= q[4] != 0.0;
+        *defect = q[1] > 0.0 ? q[0] / q[1] : q[0];
+    }
+}
+
+// Pipelined iterations: on the main branch of a body, after the norms.  If
+// the stopping rule will end the loop after this iteration (or a value is
+// non-finite), the next iteration's speculative sweep is not needed: the
+// cancel flag makes its remaining launches exit.
+__global__ void solve_eval_kernel(DevSolve *d, const double *__restrict__ norms, int has_ref,
+                                  int *cancel)
+{
+    if (threadIdx.x != 0) return;
+    double dmax, l2max, defect;
+    int bad;
+    iteration_norms(d, norms, has_ref, &dmax, &l2max, &defect, &bad);
+    const bool stop = bad || (d->stop_rule == PARAREAL_STOP_DIFF && dmax <= d->tol) ||
+                      (d->stop_rule == PARAREAL_STOP_DEFECT && defect <= d->tol);
+    if (stop) {
+        *(volatile int *)cancel = 1;
+        d->cancelled = 1;
+    }
+}
+
 // Last node of every loop pass: the stopping test after the iteration with
 // K = K0 + done exact slices -- per-slice relative changes of slices K+1..N
 // (slot s of `norms` holds {max|dU|, max|U|, sum dU^2, sum U^2,
@@ -62,21 +108,9 @@ __global__ void solve_post_kernel(DevSolve *d, const double *__restrict__ norms,
 {
     if (threadIdx.x != 0) return;
     const int N = d->N, K = d->K0 + d->done;
-    double dmax = 0.0, l2max = 0.0, defect = -1.0;
-    int bad = 0;
-    for (int s = K + 1; s <= N; ++s) {
-        const double *q = norms + 5 * s;
-        bad |= q[4] != 0.0;
-        const double di = q[1] > 0.0 ? q[0] / q[1] : q[0];
-        const double dl = q[3] > 0.0 ? sqrt(q[2] / q[3]) : sqrt(q[2]);
-        dmax = di > dmax ? di : dmax;
-        l2max = dl > l2max ? dl : l2max;
-    }
-    if (has_ref) {
-        const double *q = norms + 5 * (N + 1);
-        bad |= q[4] != 0.0;
-        defect = q[1] > 0.0 ? q[0] / q[1] : q[0];
-    }
+    double dmax, l2max, defect;
+    int bad;
+    iteration_norms(d, norms, has_ref, &dmax, &l2max, &defect, &bad);
     const int i = d->done;
     hist[4 * i + 0] = dmax;
     hist[4 * i + 1] = l2max;
@@ -101,8 +135,17 @@ struct SolveGraph {
     double *hist = nullptr;         // 4 doubles per iteration, device
     std::vector<long long> body_launches;
     bool has_ref = false;
-    int shape[12] = {0};            // launch shapes the bodies were captured with
+    int shape[16] = {0};            // launch shapes the bodies were captured with
 };
+
+// Pipelined bodies: the device-side stopping test that may cancel the
+// speculative sweep, enqueued by iter_enqueue before it joins the side branch.
+static void enqueue_eval(parareal_ctx *c, void *arg)
+{
+    SolveGraph *g = static_cast<SolveGraph *>(arg);
+    solve_eval_kernel<<<1, 32, 0, c->st>>>(g->dev, c->slice_norms, g->has_ref ? 1 : 0, c->cancel);
+    ++c->launches;
+}
 
 void solve_graph_free(parareal_ctx *c)
 {
@@ -129,9 +172,10 @@ static int expected_gcur(const parareal_ctx *c, int i, int k)
 
 static void shapes_of(const parareal_ctx *c, int *sh)
 {
-    const int v[12] = {c->fine_path, c->fine_tx, c->fine_ty, c->fine_zc,
+    const int v[16] = {c->fine_path, c->fine_tx, c->fine_ty, c->fine_zc,
                        c->ser_path, c->ser_tx, c->ser_ty, c->ser_zc,
-                       c->coarse_path, c->coarse_tx, c->coarse_ty, c->coarse_zc};
+                       c->coarse_path, c->coarse_tx, c->coarse_ty, c->coarse_zc,
+                       c->pipe_path, c->pipe_tx, c->pipe_ty, c->pipe_zc};
     std::memcpy(sh, v, sizeof v);
 }
 
@@ -143,7 +187,12 @@ static parareal_status build_graph(parareal_ctx *c)
     SolveGraph *g = new SolveGraph();
     c->sgraph = g;
     const int N = c->N;
-    CK(cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking));
+    // pipelined bodies: the chain is captured at the highest priority, the
+    // speculative sweep (side stream) at the lowest, and the graph runs with
+    // these per-node priorities
+    int lo = 0, hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CK(cudaStreamCreateWithPriority(&g->cap, cudaStreamNonBlocking, c->Fv2 ? hi : lo));
     CK(cudaMalloc((void **)&g->dev, sizeof(DevSolve)));
     CK(cudaMalloc((void **)&g->hist, sizeof(double) * 4 * (size_t)N));
     g->has_ref = c->has_ref;
@@ -214,7 +263,7 @@ static parareal_status build_graph(parareal_ctx *c)
         }
         c->k_total = K;
         const long long l0 = c->launches;
-        ps = iter_enqueue(c, false);
+        ps = iter_enqueue(c, false, true, true, enqueue_eval, g);
         g->body_launches[K] = c->launches - l0 + 2;      // with the pre and post kernels
         cudaGraph_t out = nullptr;
         const cudaError_t ee = cudaStreamEndCapture(g->cap, &out);
@@ -231,7 +280,7 @@ static parareal_status build_graph(parareal_ctx *c)
         return ps;
     }
 
-    CK(cudaGraphInstantiate(&g->exec, top, 0));
+    CK(cudaGraphInstantiate(&g->exec, top, c->Fv2 ? cudaGraphInstantiateFlagUseNodePriority : 0));
     return PARAREAL_OK;
 }
 
@@ -244,6 +293,7 @@ extern "C" parareal_status parareal_iterate_device(parareal_ctx *c, int k_max, d
     if (k_max < 0) return fail(c, PARAREAL_E_INVALID, "k_max < 0");
     if (stop_rule == PARAREAL_STOP_DEFECT && !c->has_ref) return fail(c, PARAREAL_E_STATE, "no reference set");
     if (stop_rule < 0 || stop_rule > 2) return fail(c, PARAREAL_E_INVALID, "stop_rule");
+    ChainStream chain_stream(c);
     parareal_status s;
     if (!c->started) {
         // the coarse start-up, as parareal_iterate runs it
@@ -257,7 +307,7 @@ extern "C" parareal_status parareal_iterate_device(parareal_ctx *c, int k_max, d
             return fail(c, PARAREAL_E_STATE, "iteration state not reached by parareal_iterate / "
                                              "parareal_iterate_device from set_problem");
     }
-    int sh[12];
+    int sh[16];
     shapes_of(c, sh);
     SolveGraph *g = c->sgraph;
     if (!g || g->has_ref != c->has_ref || std::memcmp(sh, g->shape, sizeof sh) != 0) {
@@ -268,6 +318,13 @@ extern "C" parareal_status parareal_iterate_device(parareal_ctx *c, int k_max, d
         }
         g = c->sgraph;
     }
+    // pipelined: every body reads the F values of its iteration from the
+    // previous body's speculative sweep; the first one's come from here
+    if (c->Fv2 && !c->spec_valid) {
+        s = fine_sweep_open(c);
+        if (s != PARAREAL_OK) return s;
+    }
+    c->spec_valid = false;
     DevSolve h{};
     h.k_max = k_max;
     h.stop_rule = stop_rule;
@@ -291,6 +348,10 @@ extern "C" parareal_status parareal_iterate_device(parareal_ctx *c, int k_max, d
     const int ran = h.status ? h.done - 1 : h.done;
     c->k_total = K0 + ran;
     for (int i = 1; i <= c->N; ++i) c->gcur[i] = expected_gcur(c, i, c->k_total);
+    // the last body's speculative sweep, unless cancelled, holds F(U^k) of the
+    // next iteration (complete: the graph joined it)
+    c->spec_valid = c->Fv2 && !h.status && !h.cancelled && h.done > 0 && c->k_total < c->N;
+    c->spec_events = false;
     if (h.done > 0) {
         const int Kl = K0 + h.done - 1;          // K of the last iteration run
         for (int sl = 0; sl <= c->N; ++sl) {

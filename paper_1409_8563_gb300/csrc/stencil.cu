@@ -500,6 +500,7 @@ rk4_fused_kernel(StepArgs a, const T *__restrict__ in, T *__restrict__ out, int 
                  int tiles_y, int zchunk, int nzc)
 {
     extern __shared__ __align__(16) unsigned char smem_fused[];
+    if (a.cancel && *(volatile const int *)a.cancel) return;    // uniform: no barrier is skipped
     int b = blockIdx.x;
     const int zc = b % nzc; b /= nzc;
     const int tx = b % tiles_x; b /= tiles_x;

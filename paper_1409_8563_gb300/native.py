@@ -49,19 +49,20 @@ class Config(ctypes.Structure):
                 ("allow_unstable", ctypes.c_int), ("learned_skip", ctypes.c_int),
                 ("fine_scheme", ctypes.c_int), ("learned_act", ctypes.c_int),
                 ("correction_form", ctypes.c_int), ("learned_eval", ctypes.c_int),
-                ("coarse_transfer", ctypes.c_int)]
+                ("coarse_transfer", ctypes.c_int), ("pipeline_blocks", ctypes.c_int)]
 
     @classmethod
     def make(cls, n, n_slices, T, dt_fine, dt_coarse, coarse_factor=1, a=(1.0, 1.0, 1.0),
              nu0=0.01, nu_amp=0.5, nu_omega=2 * np.pi, fine_dtype=F32, nu_mode=NU_STAGE,
              coarse_kind=COARSE_STENCIL, allow_unstable=0, learned_skip=0, fine_scheme=SCHEME_C2,
              learned_act=ACT_GELU, correction_form=CORRECTION_STANDARD, learned_eval=EVAL_LAYERS,
-             coarse_transfer=0):
+             coarse_transfer=0, pipeline_blocks=0):
         return cls(int(n), int(n_slices), float(T), float(dt_fine), float(dt_coarse),
                    int(coarse_factor), (ctypes.c_double * 3)(*a), float(nu0), float(nu_amp),
                    float(nu_omega), int(fine_dtype), int(nu_mode), int(coarse_kind),
                    int(allow_unstable), int(learned_skip), int(fine_scheme), int(learned_act),
-                   int(correction_form), int(learned_eval), int(coarse_transfer))
+                   int(correction_form), int(learned_eval), int(coarse_transfer),
+                   int(pipeline_blocks))
 
 
 MODEL_PARAMS = 15169
