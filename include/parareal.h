@@ -341,12 +341,26 @@ parareal_status parareal_coarse_model_grad(parareal_ctx *ctx, const float *u, co
  * (-1 when taken from the cache). */
 parareal_status parareal_autotune(parareal_ctx *ctx, const char *cache_path, double *ms2);
 
-/* The launch shapes in use, each {path (0 fused with one region row per
- * thread, 1 per-stage, 2 fused with two rows per thread), tile_x, tile_y,
- * z chunk}: the batched fine sweep, the coarse steps, and one fine
- * field at a time (serial fine run, propagate).  Any pointer may be NULL. */
+/* The launch shapes in use, each {path, tile_x, tile_y, z chunk}: the batched
+ * fine sweep, the coarse steps, and one fine field at a time (serial fine
+ * run, propagate).  Paths: 0 fused with one region row per thread, 1
+ * per-stage, 2 fused with two rows per thread, 3 persistent (every step of a
+ * sweep in one cooperative launch), 4 cluster (every step of a sweep in one
+ * launch, each field held in the shared memory of one thread-block cluster;
+ * tile_x and tile_y unused).  Paths 1, 3 and 4 give bitwise the same fields.
+ * Any pointer may be NULL.  The environment variables PARAREAL_FINE_TILE,
+ * PARAREAL_SERIAL_TILE, PARAREAL_COARSE_TILE and PARAREAL_PIPE_TILE
+ * ("path,tile_x,tile_y,zchunk") set the shapes at parareal_create. */
 parareal_status parareal_get_launch_shape(const parareal_ctx *ctx, int *fine4, int *coarse4,
                                           int *serial4);
+
+/* The number of CTAs of the cluster that holds one n^3 field of `dtype`
+ * (PARAREAL_F32 / PARAREAL_F64) in launch path 4, or 0 when the field does
+ * not fit one cluster (four n^3 arrays, three of them with a ghost plane
+ * below and above each CTA's planes, in at most 200 KiB of shared memory per
+ * CTA; planes split evenly over up to 16 CTAs where the device schedules
+ * 16-CTA clusters, else over up to 8).  No counterpart in the paper. */
+int parareal_cluster_size(int dtype, int n);
 
 /* Batches of independent problems of uneven sizes.  Each instance is a
  * context of its own (its own config, workspace and stream); one round of

@@ -216,8 +216,9 @@ static bool tile_override(const char *var, int dtype, int n, int *path, int *tx,
     if (!e || !*e) return true;
     int p, x, y, z;
     if (std::sscanf(e, "%d,%d,%d,%d", &p, &x, &y, &z) != 4) return false;
-    if (!is_fused(p) && p != PATH_STAGED && p != PATH_PERSIST) return false;
+    if (!is_fused(p) && p != PATH_STAGED && p != PATH_PERSIST && p != PATH_CLUSTER) return false;
     if (is_fused(p) && (!rk4_fused_supported(dtype, n, x, y, fused_rows(p)) || z < 1)) return false;
+    if (p == PATH_CLUSTER && rk4_cluster_size(dtype, n) == 0) return false;
     *path = p; *tx = x; *ty = y; *zc = z;
     return true;
 }
@@ -275,6 +276,10 @@ parareal_status rk4_batch(parareal_ctx *c, int m, const T *in, T *out, int first
             }
             src = dst;
         }
+    } else if (path == PATH_CLUSTER) {
+        if (op_radius(op) != 1)
+            return fail(c, PARAREAL_E_INVALID, "the cluster RK4 kernel implements radius-1 operators only");
+        LK(launch_rk4_cluster<T>(a, in, out, nsteps, c->st));
     } else if (path == PATH_PERSIST) {
         if (in != out)
             CK(cudaMemcpyAsync(out, in, (size_t)count * a.P * sizeof(T), cudaMemcpyDeviceToDevice, c->st));
@@ -783,7 +788,7 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
         if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, PARAREAL_E_CUDA, "no CUDA device");
         if (std::find(configured.begin(), configured.end(), dev) == configured.end()) {
             if (configure_rk4_kernels() != cudaSuccess || configure_spectral_kernels() != cudaSuccess ||
-                configure_queue_kernels() != cudaSuccess)
+                configure_queue_kernels() != cudaSuccess || configure_cluster_kernels() != cudaSuccess)
                 return fail(nullptr, PARAREAL_E_CUDA, "kernel configuration failed");
             configured.push_back(dev);
         }
@@ -1542,7 +1547,8 @@ static parareal_status time_shape(parareal_ctx *c, int m, int count, int path, i
 }
 
 // Candidates: every compiled fused shape (one and two rows per thread) that
-// divides m, whole-column and chunked z marches, and the per-stage path.
+// divides m, whole-column and chunked z marches, the per-stage path, the
+// persistent path, and the cluster path where the field fits one cluster.
 enum { NO_STAGED = 1, NO_PERSIST = 2 };
 
 static void candidates(int dtype, int m, std::vector<std::array<int, 4>> *out, int exclude = 0)
@@ -1558,6 +1564,8 @@ static void candidates(int dtype, int m, std::vector<std::array<int, 4>> *out, i
         }
     if (!(exclude & NO_STAGED)) out->push_back({PATH_STAGED, 16, 8, m});
     if (!(exclude & NO_PERSIST)) out->push_back({PATH_PERSIST, 16, 8, m});
+    if (!(exclude & NO_STAGED) && rk4_cluster_size(dtype, m) > 0)
+        out->push_back({PATH_CLUSTER, 0, 0, m});
 }
 
 static std::string tune_key(int dtype, int m, int count, int exclude)
@@ -1566,7 +1574,9 @@ static std::string tune_key(int dtype, int m, int count, int exclude)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     char k[128];
-    std::snprintf(k, sizeof k, "n=%d dtype=%d count=%d sms=%d%s%s", m, dtype, count, sms,
+    // "paths=5": the candidate set includes launch paths 0-4 (a cached pick
+    // made from fewer paths is not reused)
+    std::snprintf(k, sizeof k, "n=%d dtype=%d count=%d sms=%d paths=5%s%s", m, dtype, count, sms,
                   (exclude & NO_STAGED) ? " nostaged" : "", (exclude & NO_PERSIST) ? " nopersist" : "");
     return k;
 }
@@ -1610,6 +1620,7 @@ static parareal_status tune_one(parareal_ctx *c, const char *cache, int m, int c
     if (cache_lookup(cache, key, sh) &&
         ((sh[0] == PATH_STAGED && !(exclude & NO_STAGED)) ||
          (sh[0] == PATH_PERSIST && !(exclude & NO_PERSIST)) ||
+         (sh[0] == PATH_CLUSTER && !(exclude & NO_STAGED) && rk4_cluster_size(dtype, m) > 0) ||
          (is_fused(sh[0]) && rk4_fused_supported(dtype, m, sh[1], sh[2], fused_rows(sh[0]))))) {
         *path = sh[0]; *tx = sh[1]; *ty = sh[2]; *zc = sh[3];
         *best_ms = -1.0;
@@ -1693,6 +1704,12 @@ extern "C" parareal_status parareal_autotune(parareal_ctx *c, const char *cache_
     c->has_problem = false;   // the iterate was used as scratch
     c->started = false;
     return PARAREAL_OK;
+}
+
+extern "C" int parareal_cluster_size(int dtype, int n)
+{
+    if ((dtype != PARAREAL_F32 && dtype != PARAREAL_F64) || n < 4) return 0;
+    return rk4_cluster_size(dtype, n);
 }
 
 extern "C" parareal_status parareal_get_launch_shape(const parareal_ctx *c, int *fine4, int *coarse4,

@@ -13,7 +13,7 @@
 // thread, the per-stage kernels, the fused kernel with two rows per thread,
 // and the per-stage arithmetic as one persistent cooperative launch per
 // sweep (grid barriers between stages; small grids).
-enum { PATH_FUSED = 0, PATH_STAGED = 1, PATH_FUSED2 = 2, PATH_PERSIST = 3 };
+enum { PATH_FUSED = 0, PATH_STAGED = 1, PATH_FUSED2 = 2, PATH_PERSIST = 3, PATH_CLUSTER = 4 };
 // region rows per thread of a fused launch path
 inline int fused_rows(int path) { return path == PATH_FUSED2 ? 2 : 1; }
 inline bool is_fused(int path) { return path == PATH_FUSED || path == PATH_FUSED2; }

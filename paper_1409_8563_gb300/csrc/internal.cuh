@@ -90,6 +90,12 @@ __host__ __device__ inline void op_weights(int op, double nu, double dt, int n, 
     }
 }
 
+// nu(t) = nu0 (1 + nu_amp sin(nu_omega t)) (Sec. 3), in FP64.
+__device__ __forceinline__ double nu_at(const StepArgs &a, double t)
+{
+    return a.nu0 * (1.0 + a.nu_amp * sin(a.nu_omega * t));
+}
+
 // Streaming multiprocessors of the current device (cached per device).
 int sm_count();
 
@@ -161,6 +167,20 @@ cudaError_t launch_rk4_persist(const StepArgs &a, T *u, T *y1, T *y2, T *acc, lo
 // Self-test: a cooperative launch in which one block never reaches the grid
 // barrier (every other block's bounded wait gives up and sets b->err).
 cudaError_t launch_grid_barrier_selftest(GridBarrier *b, cudaStream_t st);
+
+// All nsteps RK4 steps of `count` small fields (7-point operator) in one
+// launch, each field held in the distributed shared memory of one
+// thread-block cluster (planes split along z over the cluster's CTAs, z
+// neighbours of a CTA's edge planes read from its neighbours' shared
+// memory, a cluster barrier between stages): the per-point arithmetic of
+// launch_rk4_stage, so the result equals the per-stage path's bit for bit.
+// in may equal out.  a.j is ignored (steps 0..nsteps-1 of the slice).
+template <typename T>
+cudaError_t launch_rk4_cluster(const StepArgs &a, const T *in, T *out, long long nsteps,
+                               cudaStream_t st);
+// The cluster size for an n^3 field of `dtype` (0: the field does not fit).
+int rk4_cluster_size(int dtype, int n);
+cudaError_t configure_cluster_kernels();
 
 // The fine sweeps of up to QUEUE_MAX problems in one launch: CTAs take tile
 // steps from the queue in order (head: a device counter, zeroed before the

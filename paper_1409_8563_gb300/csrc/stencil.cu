@@ -82,10 +82,6 @@ __device__ __forceinline__ void stv<double>(double *p, const double (&r)[2])
     *reinterpret_cast<double2 *>(p) = make_double2(r[0], r[1]);
 }
 
-__device__ __forceinline__ double nu_at(const StepArgs &a, double t)
-{
-    return a.nu0 * (1.0 + a.nu_amp * sin(a.nu_omega * t));
-}
 
 template <typename T, int TX, int TY, int R>
 struct FusedShape {

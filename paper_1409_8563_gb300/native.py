@@ -83,6 +83,7 @@ _vp, _cp, _i, _d, _dp, _ip = (ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int, ct
                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int))
 SIGNATURES = {
     "parareal_create": (_i, [ctypes.POINTER(Config), _vp, ctypes.POINTER(_vp)]),
+    "parareal_cluster_size": (_i, [_i, _i]),
     "parareal_stability": (_i, [ctypes.POINTER(Config), _dp]),
     "parareal_set_problem": (_i, [_vp, _vp, _i, _i]),
     "parareal_fine_sweep": (_i, [_vp, _i, _i]),
@@ -182,6 +183,11 @@ def stability(cfg):
     g = (ctypes.c_double * 2)()
     st = lib().parareal_stability(ctypes.byref(cfg), g)
     return st, (g[0], g[1])
+
+
+def cluster_size(dtype, n):
+    """CTAs of the cluster that holds one n^3 field in launch path 4 (0: does not fit)."""
+    return int(lib().parareal_cluster_size(int(dtype), int(n)))
 
 
 class Parareal:
