@@ -167,8 +167,18 @@ enum { PARAREAL_ACT_GELU = 0, PARAREAL_ACT_LINEAR = 1 };
  *          cross-correlation per slice, K_0 + nu(t_n)/nu0 K_1 (built in FP64
  *          from the FP32 master weights whenever the model changes), applied
  *          with FP32 accumulation: the same linear operator in about a
- *          twentieth of the arithmetic.  No counterpart in the paper. */
-enum { PARAREAL_EVAL_LAYERS = 0, PARAREAL_EVAL_COMPOSED = 1 };
+ *          twentieth of the arithmetic.
+ * POLYPHASE with the stencil skip on a coarsened grid (coarse_factor r in
+ *          {2, 4, 8}, BOX transfers, n a multiple of 16): the composed kernel
+ *          and the skip's trilinear prolongation folded into r^3 phase
+ *          kernels on the coarse grid (4^3 taps each for r = 4, 3^3 for
+ *          r = 8, 6^3 for r = 2; built in FP64, applied in G's precision with
+ *          FP32 weights).  G's output then stays on the coarse grid, as the
+ *          stencil propagator's does, and the correction prolongs the change
+ *          of G's output through the phase kernels: G costs about what the
+ *          stencil propagator costs.  The same linear operator as COMPOSED.
+ *          No counterpart in the paper. */
+enum { PARAREAL_EVAL_LAYERS = 0, PARAREAL_EVAL_COMPOSED = 1, PARAREAL_EVAL_POLYPHASE = 2 };
 
 /* Evaluation of the correction (Eq. parareal):
  * STANDARD   U^{k+1}[n+1] = F(U^k[n]) + (G(U^{k+1}[n]) - G(U^k[n])), as printed;

@@ -123,9 +123,17 @@ static parareal_status validate(const parareal_config *cfg, long long *Nf, long 
         return PARAREAL_E_INVALID;
     }
     if (cfg->learned_skip != PARAREAL_SKIP_SHIFT && cfg->learned_skip != PARAREAL_SKIP_STENCIL) { *msg = "learned_skip"; return PARAREAL_E_INVALID; }
-    if (cfg->learned_eval != PARAREAL_EVAL_LAYERS && cfg->learned_eval != PARAREAL_EVAL_COMPOSED) { *msg = "learned_eval"; return PARAREAL_E_INVALID; }
-    if (cfg->learned_eval == PARAREAL_EVAL_COMPOSED && cfg->learned_act != PARAREAL_ACT_LINEAR) {
-        *msg = "learned_eval COMPOSED needs learned_act LINEAR (a GELU network is not one convolution)";
+    if (cfg->learned_eval != PARAREAL_EVAL_LAYERS && cfg->learned_eval != PARAREAL_EVAL_COMPOSED &&
+        cfg->learned_eval != PARAREAL_EVAL_POLYPHASE) { *msg = "learned_eval"; return PARAREAL_E_INVALID; }
+    if (cfg->learned_eval != PARAREAL_EVAL_LAYERS && cfg->learned_act != PARAREAL_ACT_LINEAR) {
+        *msg = "learned_eval COMPOSED / POLYPHASE needs learned_act LINEAR (a GELU network is not one convolution)";
+        return PARAREAL_E_INVALID;
+    }
+    if (cfg->learned_eval == PARAREAL_EVAL_POLYPHASE && cfg->coarse_kind == PARAREAL_COARSE_LEARNED &&
+        (cfg->learned_skip != PARAREAL_SKIP_STENCIL || (cfg->coarse_factor != 2 && cfg->coarse_factor != 4 &&
+                                                        cfg->coarse_factor != 8) ||
+         cfg->coarse_transfer != PARAREAL_TRANSFER_BOX || cfg->n % 16)) {
+        *msg = "learned_eval POLYPHASE needs the stencil skip, coarse_factor 2, 4 or 8, box transfers and n a multiple of 16";
         return PARAREAL_E_INVALID;
     }
     if (cfg->coarse_transfer != PARAREAL_TRANSFER_BOX && cfg->coarse_transfer != PARAREAL_TRANSFER_SPECTRAL) { *msg = "coarse_transfer"; return PARAREAL_E_INVALID; }
@@ -442,7 +450,8 @@ static parareal_status coarse_apply_t(parareal_ctx *c, const double *Uin, int s,
         return euler_batch<T>(c, c->n, reinterpret_cast<const T *>(Uin), static_cast<T *>(out), s, 1,
                               c->Nc, c->cfg.dt_coarse, OP_UPWIND, cB, cC);
     }
-    if (c->cfg.coarse_kind != PARAREAL_COARSE_STENCIL) {
+    // the phase-kernel learned G: its coarse part is the stencil propagator's
+    if (c->cfg.coarse_kind != PARAREAL_COARSE_STENCIL && !c->net.poly) {
         if (c->cfg.learned_skip == PARAREAL_SKIP_STENCIL) {
             // the net corrects the stencil propagator's output on the fine grid
             double *gs = c->tmpd + c->P;
@@ -484,9 +493,17 @@ static parareal_status coarse_apply_t(parareal_ctx *c, const double *Uin, int s,
 // (trilinear inside the correction kernel, or the spectral prolongation into
 // a fine T field first).  Fv / cold may be null.
 template <typename T>
-static parareal_status correct_coarse(parareal_ctx *c, const T *Fv, const T *cnew, const T *cold,
+static parareal_status correct_coarse(parareal_ctx *c, int s, const T *Fv, const T *cnew, const T *cold,
                                       double *U, double *dU)
 {
+    if (c->net.poly) {
+        // the learned G's change through slice s's phase kernels
+        T *fine = static_cast<T *>(c->sp_fine);
+        LK(launch_poly_prolong<T>(cnew, cold, c->net.wpoly + poly_weights_floats(c->r, s), c->n, c->r, fine,
+                                  c->st));
+        LK((launch_correct<T, T>(Fv, fine, nullptr, U, c->n, 1, c->partials, c->nblk, c->st, dU)));
+        return PARAREAL_OK;
+    }
     if (!c->spectral) {
         LK((launch_correct<T, T>(Fv, cnew, cold, U, c->n, c->r, c->partials, c->nblk, c->st, dU)));
         return PARAREAL_OK;
@@ -509,7 +526,7 @@ static parareal_status correct_t(parareal_ctx *c, int s, const void *gnew, const
                             : nullptr;
     double *U = c->U + (long long)(s + 1) * c->P;
     if (!c->g_fine) {
-        parareal_status ps = correct_coarse<T>(c, Fv, static_cast<const T *>(gnew),
+        parareal_status ps = correct_coarse<T>(c, s, Fv, static_cast<const T *>(gnew),
                                                static_cast<const T *>(gold), U, dU);
         if (ps != PARAREAL_OK) return ps;
     } else {
@@ -838,8 +855,9 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
     const size_t P = (size_t)c->P, Pc = (size_t)c->Pc, N = (size_t)c->N;
     // G's output: a coarse T field when G ends on the coarse grid (stencil G,
     // or a net on the restricted grid), else a fine FP64 field
+    const bool poly = cfg->coarse_kind == PARAREAL_COARSE_LEARNED && cfg->learned_eval == PARAREAL_EVAL_POLYPHASE;
     c->g_fine = c->r == 1 || (cfg->coarse_kind != PARAREAL_COARSE_STENCIL &&
-                              cfg->learned_skip == PARAREAL_SKIP_STENCIL);
+                              cfg->learned_skip == PARAREAL_SKIP_STENCIL && !poly);
     const size_t gbytes = c->g_fine ? P * sizeof(double) : Pc * e;
     bool ok = cudaGetDevice(&c->dev) == cudaSuccess;
     ok = ok && alloc((void **)&c->U, (N + 1) * P * sizeof(double));
@@ -887,6 +905,8 @@ extern "C" parareal_status parareal_create(const parareal_config *cfg, void *str
     ok = ok && alloc((void **)&c->bar, sizeof(pr::GridBarrier)) &&
          cudaMemset(c->bar, 0, sizeof(pr::GridBarrier)) == cudaSuccess;
     c->spectral = cfg->coarse_transfer == PARAREAL_TRANSFER_SPECTRAL;
+    // the fine field a coarse G's change is prolonged into before the correction
+    if (poly) ok = ok && alloc(&c->sp_fine, P * e);
     if (c->spectral) {
         const size_t me = (size_t)c->n * c->nc * e;
         ok = ok && alloc(&c->sp_R, me) && alloc(&c->sp_Rt, me) && alloc(&c->sp_P, me) &&
@@ -1484,7 +1504,7 @@ static parareal_status propagate_t(parareal_ctx *c, int which, const void *src, 
             CK(cudaMemsetAsync(res64, 0, P * 8, c->st));
             const T *nullT = nullptr;
             if (!c->g_fine) {
-                s = correct_coarse<T>(c, nullT, static_cast<const T *>(c->gspare), nullptr, res64,
+                s = correct_coarse<T>(c, first + f, nullT, static_cast<const T *>(c->gspare), nullptr, res64,
                                       nullptr);
                 if (s != PARAREAL_OK) return s;
             } else {

@@ -43,6 +43,9 @@ struct NetState {
     bool composed = false;     // linear mode evaluated as one 9^3 kernel per slice
     double *kscratch = nullptr;             // composition scratch (device)
     float *keff = nullptr;                  // per-slice 9^3 kernels (device)
+    bool poly = false;         // ... folded with the prolongation into phase kernels
+    double *wpoly2 = nullptr;               // FP64 phase kernels of K_0 (+ skip) and K_1
+    float *wpoly = nullptr;                 // per-slice FP32 phase kernels
     bool tc = false;           // 16 -> 16 layers on tcgen05 (grid edge a multiple of 16)
     int *tc_err = nullptr;     // device flag: a tensor-core completion wait ran out
     bool has_model = false;

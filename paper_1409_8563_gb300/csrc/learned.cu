@@ -62,12 +62,18 @@ parareal_status net_setup(parareal_ctx *c)
               dalloc((void **)&S.B4f, 27 * 8 * 16 * 2) && dalloc((void **)&S.tc_err, sizeof(int)) &&
               dalloc((void **)&S.nu_slices, sizeof(float) * c->N) &&
               dalloc((void **)&S.ia, (size_t)S.Pm * 32) && dalloc((void **)&S.ib, (size_t)S.Pm * 32);
-    S.composed = S.lin && c->cfg.learned_eval == PARAREAL_EVAL_COMPOSED;
+    S.composed = S.lin && c->cfg.learned_eval != PARAREAL_EVAL_LAYERS;
+    S.poly = S.lin && c->cfg.learned_eval == PARAREAL_EVAL_POLYPHASE && stencil_skip && c->r > 1;
     if (S.composed && S.m % 16)
         return fail(c, PARAREAL_E_INVALID, "the composed learned propagator needs a grid edge that is a multiple of 16");
     if (ok && S.composed)
         ok = dalloc((void **)&S.kscratch, compose_scratch_doubles() * sizeof(double)) &&
              dalloc((void **)&S.keff, sizeof(float) * NET_K9 * c->N);
+    if (ok && S.poly) {
+        ok = dalloc((void **)&S.wpoly2, poly_scratch_doubles(c->r) * sizeof(double)) &&
+             dalloc((void **)&S.wpoly, poly_weights_floats(c->r, c->N) * sizeof(float));
+        CK(configure_poly_kernels(c->r));
+    }
     if (!ok) return fail(c, PARAREAL_E_NOMEM, "learned propagator allocation failed");
     std::vector<float> nus(c->N);
     for (int s = 0; s < c->N; ++s) nus[s] = (float)(nu_of(c->cfg, s * slice) / c->cfg.nu0);
@@ -89,6 +95,8 @@ parareal_status net_compose(parareal_ctx *c)
     NetState &S = c->net;
     if (!S.composed) return PARAREAL_OK;
     LK(launch_compose_linear(S.master, S.nu_slices, c->N, S.kscratch, S.keff, c->st));
+    if (S.poly)
+        LK(launch_compose_poly(composed_kernels(S.kscratch), c->r, S.nu_slices, c->N, S.wpoly2, S.wpoly, c->st));
     return PARAREAL_OK;
 }
 
@@ -97,7 +105,8 @@ void net_free(parareal_ctx *c)
     NetState &S = c->net;
     void *p[] = {S.master, S.grad, S.mom1, S.mom2, S.W1q, S.W4q, S.B2f, S.B3f, S.B2b, S.B3b, S.B4f, S.tc_err,
                  S.nu_slices, S.ia, S.ib, S.z1, S.z2, S.z3, S.a1, S.a2, S.a3, S.dzA, S.dzB, S.dz4,
-                 S.ub, S.fb, S.nub, S.partials, S.loss_parts, S.loss_sum, S.kscratch, S.keff};
+                 S.ub, S.fb, S.nub, S.partials, S.loss_parts, S.loss_sum, S.kscratch, S.keff,
+                 S.wpoly2, S.wpoly};
     for (void *q : p)
         if (q) cudaFree(q);
     if (S.h_nub) cudaFreeHost(S.h_nub);

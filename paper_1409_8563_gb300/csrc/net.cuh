@@ -28,6 +28,26 @@ cudaError_t launch_compose_linear(const float *master, const float *nu_hat, int 
 // device, FP32 accumulation; m a multiple of 16.
 template <typename TU, typename TG>
 cudaError_t launch_net_lin9(const TU *u, int m, const int s[3], const float *K, TG *out, cudaStream_t st);
+// After launch_compose_linear: the two composed 9^3 kernels K_0, K_1 in FP64
+// ([2][NET_K9], index (ez+4) 81 + (ey+4) 9 + (ex+4)) inside its scratch.
+const double *composed_kernels(const double *scratch);
+
+// net_poly.cu: the stencil-skip LINEAR propagator as r^3 phase kernels on the
+// coarse grid.  TT taps per axis, lo_off the lowest coarse offset a tap
+// reaches, win the coarse window edge of one 16^3 fine brick.
+void poly_geometry(int r, int *TT, int *lo_off, int *win);
+size_t poly_weights_floats(int r, int n_slices);   // per-slice FP32 phase kernels
+size_t poly_scratch_doubles(int r);                 // FP64 phase kernels of K_0 and K_1
+cudaError_t configure_poly_kernels(int r);
+// W2 (FP64) from K2 = composed_kernels(...), then Wn (FP32, per slice).
+cudaError_t launch_compose_poly(const double *K2, int r, const float *nu_hat, int n_slices, double *W2,
+                                float *Wn, cudaStream_t st);
+// out = (phase kernels of one slice, Wn + slice offset) applied to cnew - cold
+// (cold may be null) on the coarse grid of edge n / r; out is the fine n^3
+// field.  n a multiple of 16, r in {2, 4, 8, 16}.
+template <typename T>
+cudaError_t launch_poly_prolong(const T *cnew, const T *cold, const float *W, int n, int r, T *out,
+                                cudaStream_t st);
 
 cudaError_t configure_net_kernels();
 // 16 -> 16 forward layer on the 5th-generation tensor cores (net_tc.cu);

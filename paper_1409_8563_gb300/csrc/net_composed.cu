@@ -89,6 +89,8 @@ cudaError_t launch_compose_linear(const float *master, const float *nu_hat, int 
 
 size_t compose_scratch_doubles() { return 2 * (size_t)COMPOSE_MAX; }
 
+const double *composed_kernels(const double *scratch) { return scratch + COMPOSE_MAX; }
+
 // out[p] = x[p] + sum_e K[e] x[p + e], x = S(u), S(u)[q] = u[q - s] (periodic
 // shift s in [0, m)^3), K the slice's kernel in device memory.  One CTA of
 // 128 threads per 8 x 8 x 16 output tile: the 16 x 16 x 24 halo of x in

@@ -22,7 +22,7 @@ COARSE_STENCIL, COARSE_LEARNED, COARSE_SHIFT, COARSE_EULER_UPWIND = 0, 1, 2, 3
 SCHEME_C2, SCHEME_C4 = 0, 1
 ACT_GELU, ACT_LINEAR = 0, 1
 CORRECTION_STANDARD, CORRECTION_DIFFERENCE = 0, 1
-EVAL_LAYERS, EVAL_COMPOSED = 0, 1
+EVAL_LAYERS, EVAL_COMPOSED, EVAL_POLYPHASE = 0, 1, 2
 SKIP_SHIFT, SKIP_STENCIL = 0, 1
 TRANSFER_BOX, TRANSFER_SPECTRAL = 0, 1
 STOP_DIFF, STOP_DEFECT, STOP_NONE = 0, 1, 2
