@@ -732,7 +732,13 @@ def run_learned_128(args):
     composed.set_coarse_model(linear.get_coarse_model())
     u = torch.from_numpy(u0).cuda()
     res = {}
-    ctxs = {"learned_linear_composed": composed,
+    # ... and folded with the prolongation into phase kernels on the coarse grid
+    poly = native.Parareal(mk(native.COARSE_LEARNED, base.coarse_factor, base.dt_coarse,
+                              native.SKIP_STENCIL, native.ACT_LINEAR,
+                              native.CORRECTION_DIFFERENCE, native.EVAL_POLYPHASE))
+    poly.set_coarse_model(linear.get_coarse_model())
+    ctxs = {"learned_linear_polyphase": poly,
+            "learned_linear_composed": composed,
             "learned_linear": linear,
             "learned_gelu": learned,
             "stencil": native.Parareal(base),
@@ -819,8 +825,9 @@ def run_learned_512(args):
     ref = torch.empty((n,) * 3, dtype=torch.float64, device="cuda")
     runs = {}
     for name, kind in (("stencil_difference_form", native.COARSE_STENCIL),
-                       ("learned_linear_composed", native.COARSE_LEARNED)):
-        c = native.Parareal(mk(kind, native.EVAL_COMPOSED if kind == native.COARSE_LEARNED
+                       ("learned_linear_polyphase", native.COARSE_LEARNED)):
+        # the trained linear net folded with the prolongation into phase kernels
+        c = native.Parareal(mk(kind, native.EVAL_POLYPHASE if kind == native.COARSE_LEARNED
                                else native.EVAL_LAYERS))
         c.autotune(TUNE_CACHE)
         if kind == native.COARSE_LEARNED:
