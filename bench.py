@@ -14,6 +14,12 @@ fused RK4 kernel from CUDA-event timing of its launches inside the timed
 region, the end-to-end number through the C ABI with host buffers, and the
 FP64 CPU oracle timed on this host.
 
+The default line also carries three comparisons, each with its own clock
+record: the 128^3 learned-vs-stencil propagator (c4_learned_128), the 64
+uneven instances (c3_batch64) and the 32^3 FP64 plain method, the
+latency-bound regime in which the slices batched on one GPU can beat serial
+fine stepping (c1_fp64_32).
+
 ``--impl reference`` times the CPU oracle instead (the only reference this
 method has), on a bounded sample of the same workload.
 """
@@ -477,8 +483,10 @@ def run(args):
     if rank == 0 and world == 1 and args.workload == "fp32_256" and not args.no_c4:
         line["c4_learned_128"] = c4_learned_128(local, pipeline=args.pipeline)
     if rank == 0 and world == 1 and args.workload == "fp32_256" and not args.no_c3:
-        line["c3_batch64"] = {m: batch64(args.correction, m == "queue", 1, 1)
+        line["c3_batch64"] = {m: batch64(args.correction, m == "queue", 1, 1, local)
                               for m in ("graph", "queue")}
+    if rank == 0 and world == 1 and args.workload == "fp32_256" and not args.no_c1:
+        line["c1_fp64_32"] = fp64_32(local, steps=20, warmup=3)
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -597,35 +605,45 @@ def _timed(fn, reps=1):
     return (time.perf_counter() - t0) * 1000 / reps, out
 
 
-def run_fp64_32(args):
-    """32^3 FP64, N = 8: time-to-1e-6 Parareal vs serial fine."""
+def fp64_32(dev_index, steps=5, warmup=3):
+    """32^3 FP64, N = 8 (the paper-scale plain method): time-to-1e-6 of
+    Parareal (host and device iteration loops) against serial fine, the
+    latency-bound regime where one GPU's batched slices can win."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_1409_8563_gb300 import configs, native
     cfg, u0 = configs.plain_fp64_32()
     ctx = native.Parareal(cfg)
     u = torch.from_numpy(u0).cuda()
     ctx.set_problem(u)
     ctx.serial_fine(None, as_reference=True)
-    serial_ms, _ = _timed(lambda: ctx.serial_fine(None, as_reference=True), 3)
 
     def solve(device=False):
         ctx.set_problem(u)
         return ctx.iterate(cfg.n_slices, TOL, native.STOP_DEFECT, device=device)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         solve()
         solve(True)
-    ms, (k, h) = _timed(solve, args.steps)
-    ms_dev, _ = _timed(lambda: solve(True), args.steps)
+    with ClockSampler(dev_index) as clk:
+        serial_ms, _ = _timed(lambda: ctx.serial_fine(None, as_reference=True), steps)
+        ms, (k, h) = _timed(solve, steps)
+        ms_dev, (k_dev, _) = _timed(lambda: solve(True), steps)
     P, N, nf = 32 ** 3, cfg.n_slices, round(cfg.T / cfg.n_slices / cfg.dt_fine)
     ups = sum(N - j for j in range(k)) * P * nf
-    print(json.dumps({"workload": "fp64_32", "time_to_1e-6_ms": ms, "serial_fine_ms": serial_ms,
-                      "time_to_1e-6_device_loop_ms": ms_dev,
-                      "parareal_over_serial": ms / serial_ms, "k_star": k,
-                      "defects": [float(x) for x in h[:, 2]], "glups_in_solve": ups / ms / 1e6,
-                      "dtype": "f64", "steps": args.steps, "warmup": args.warmup}))
+    out = {"workload": "fp64_32: 32^3 FP64, N=8, dt_F=1/1024, G = same grid at 1/64, 8 Fourier modes",
+           "time_to_1e-6_ms": ms, "serial_fine_ms": serial_ms,
+           "time_to_1e-6_device_loop_ms": ms_dev, "k_star_device_loop": int(k_dev),
+           "parareal_over_serial": ms / serial_ms,
+           "parareal_device_loop_over_serial": ms_dev / serial_ms, "k_star": int(k),
+           "defects": [float(x) for x in h[:, 2]], "glups_in_solve": ups / ms / 1e6,
+           "dtype": "f64", "steps": steps, "warmup": warmup, "clocks": clk.summary()}
     ctx.close()
+    return out
+
+
+def run_fp64_32(args):
+    import __graft_entry__
+    __graft_entry__.build()
+    print(json.dumps(fp64_32(0, args.steps, args.warmup)))
     return 0
 
 
@@ -889,7 +907,7 @@ def run_learned_g(args):
     return 0
 
 
-def batch64(correction="difference", queue=False, steps=1, warmup=1):
+def batch64(correction="difference", queue=False, steps=1, warmup=1, dev_index=0):
     """64 uneven instances (sizes from {32,48,64,96,128}, nu0 in [0.002, 0.02],
     N = 8, T = 1) solved to a defect of 1e-6: one CUDA graph per round, the
     fine sweeps as each instance's own launches (graph mode) or as one
@@ -913,7 +931,6 @@ def batch64(correction="difference", queue=False, steps=1, warmup=1):
     for i, u in enumerate(u0s):
         b.set_problem(i, u)
     b.serial_fine(True)
-    serial_ms, _ = _timed(lambda: b.serial_fine(True), 1)
 
     def solve():
         for i, u in enumerate(u0s):
@@ -921,7 +938,9 @@ def batch64(correction="difference", queue=False, steps=1, warmup=1):
         return b.iterate(8, TOL, native.STOP_DEFECT)
     for _ in range(max(warmup, 1)):
         solve()
-    ms, (k, d) = _timed(solve, max(steps, 1))
+    with ClockSampler(dev_index) as clk:
+        serial_ms, _ = _timed(lambda: b.serial_fine(True), 1)
+        ms, (k, d) = _timed(solve, max(steps, 1))
     ups = 0
     for cfg, kk in zip(cfgs, k):
         nf = round(cfg.T / cfg.n_slices / cfg.dt_fine)
@@ -932,7 +951,7 @@ def batch64(correction="difference", queue=False, steps=1, warmup=1):
            "k_star": [int(x) for x in k], "max_defect": float(max(d)),
            "glups_in_solve": ups / ms / 1e6, "autotune_ms": tune_ms,
            "correction_form": correction, "fine_shape": list(b.fine_mode()),
-           "graph_launches": b.graph_launches()}
+           "graph_launches": b.graph_launches(), "clocks": clk.summary()}
     b.close()
     del u0s
     torch.cuda.empty_cache()
@@ -995,6 +1014,8 @@ def main():
                          "blocks on a second stream while the coarse chain runs (0: off)")
     ap.add_argument("--no-c3", action="store_true",
                     help="fp32_256: leave out the 64-instance batch comparison (graph and queue modes)")
+    ap.add_argument("--no-c1", action="store_true",
+                    help="fp32_256: leave out the 32^3 FP64 comparison (Parareal vs serial fine)")
     ap.add_argument("--no-c4", action="store_true",
                     help="skip the 128^3 learned-propagator comparison of the default line")
     ap.add_argument("--workload", default="fp32_256",

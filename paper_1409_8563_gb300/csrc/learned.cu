@@ -144,8 +144,8 @@ parareal_status net_apply(parareal_ctx *c, const TU *u, int slice, TG *out)
     LK(launch_net_in_fwd<TU>(u, S.m, S.shift, S.nu_slices + slice, 1, S.W1q, b + NET_B1, nullptr, S.ia, c->st,
                              S.lin));
     if (S.tc) {
-        LK(launch_net_mid_tc(S.ia, S.m, 1, S.B2f, b + NET_B2, S.ib, S.lin, S.tc_err, c->st));
-        LK(launch_net_mid_tc(S.ib, S.m, 1, S.B3f, b + NET_B3, S.ia, S.lin, S.tc_err, c->st));
+        LK(launch_net_mid_tc(0, S.ia, S.m, 1, S.B2f, b + NET_B2, nullptr, nullptr, S.ib, S.lin, S.tc_err, c->st));
+        LK(launch_net_mid_tc(0, S.ib, S.m, 1, S.B3f, b + NET_B3, nullptr, nullptr, S.ia, S.lin, S.tc_err, c->st));
     } else {
         LK(launch_net_mid(0, S.ia, S.m, 1, S.B2f, b + NET_B2, nullptr, nullptr, S.ib, c->st, S.lin));
         LK(launch_net_mid(0, S.ib, S.m, 1, S.B3f, b + NET_B3, nullptr, nullptr, S.ia, c->st, S.lin));
@@ -190,6 +190,30 @@ static parareal_status net_training_buffers(parareal_ctx *c, int batch)
     return PARAREAL_OK;
 }
 
+// One 16 -> 16 layer of training, forward (mode 0, pre-activations into zout)
+// or input gradient (mode 1, mirrored operand, times gelu'(zaux)): on the
+// tensor cores (tcgen05) where the grid edge allows their tiles, else the
+// mma.sync kernel.
+static cudaError_t mid_layer(parareal_ctx *c, int mode, const __nv_bfloat16 *in, int batch,
+                             const __nv_bfloat16 *Bt, const float *bias, const float *zaux, float *zout,
+                             __nv_bfloat16 *out)
+{
+    NetState &S = c->net;
+    if (S.tc)
+        return launch_net_mid_tc(mode, in, S.m, batch, Bt, bias, zaux, zout, out, S.lin, S.tc_err, c->st);
+    return launch_net_mid(mode, in, S.m, batch, Bt, bias, zaux, zout, out, c->st, S.lin);
+}
+
+// Weight-gradient partials of a 16 -> 16 layer (input x, output gradient dz),
+// on the tensor cores where the forward runs there.
+static cudaError_t mid_wgrad(parareal_ctx *c, const __nv_bfloat16 *x, const __nv_bfloat16 *dz, int batch,
+                             int nb)
+{
+    NetState &S = c->net;
+    if (S.tc) return launch_net_mid_wgrad_tc(x, dz, S.m, batch, S.partials, nb, S.tc_err, c->st);
+    return launch_net_mid_wgrad(x, dz, S.m, batch, S.partials, nb, c->st);
+}
+
 // Loss and gradient of one batch already staged in S.ub / S.fb / S.nub;
 // the loss sum lands in loss_slot (device).  grad = d(mean squared error)/dparams.
 static parareal_status net_loss_grad(parareal_ctx *c, int batch, double *loss_slot)
@@ -202,8 +226,8 @@ static parareal_status net_loss_grad(parareal_ctx *c, int batch, double *loss_sl
     // forward, keeping pre-activations
     LK(launch_net_in_fwd<float>(S.ub, m, S.shift, S.nub, batch, S.W1q, b + NET_B1, S.z1, S.a1, c->st,
                                 S.lin));
-    LK(launch_net_mid(0, S.a1, m, batch, S.B2f, b + NET_B2, nullptr, S.z2, S.a2, c->st, S.lin));
-    LK(launch_net_mid(0, S.a2, m, batch, S.B3f, b + NET_B3, nullptr, S.z3, S.a3, c->st, S.lin));
+    LK(mid_layer(c, 0, S.a1, batch, S.B2f, b + NET_B2, nullptr, S.z2, S.a2));
+    LK(mid_layer(c, 0, S.a2, batch, S.B3f, b + NET_B3, nullptr, S.z3, S.a3));
     const float gscale = (float)(2.0 / (double)F);
     LK((launch_net_out_fwd<float, float>(S.a3, m, batch, S.W4q, b + NET_B4, S.ub, S.shift, nullptr,
                                          S.fb, gscale, S.dz4, S.loss_parts, c->st, S.lin)));
@@ -213,12 +237,12 @@ static parareal_status net_loss_grad(parareal_ctx *c, int batch, double *loss_sl
     LK(launch_net_out_wgrad(S.a3, S.dz4, m, batch, S.partials, nb, c->st));
     LK(launch_reduce_cols(S.partials, nb, NET_OUT_PARTIAL, NET_OUT_PARTIAL, S.grad + NET_W4, c->st));
     LK(launch_net_out_dgrad(S.dz4, m, batch, S.W4q, S.z3, S.dzA, c->st, S.lin));   // dz3
-    LK(launch_net_mid_wgrad(S.a2, S.dzA, m, batch, S.partials, nb, c->st));
+    LK(mid_wgrad(c, S.a2, S.dzA, batch, nb));
     LK(launch_reduce_mid(S.partials, nb, S.grad + NET_W3, S.grad + NET_B3, c->st));
-    LK(launch_net_mid(1, S.dzA, m, batch, S.B3b, nullptr, S.z2, nullptr, S.dzB, c->st, S.lin));  // dz2
-    LK(launch_net_mid_wgrad(S.a1, S.dzB, m, batch, S.partials, nb, c->st));
+    LK(mid_layer(c, 1, S.dzA, batch, S.B3b, nullptr, S.z2, nullptr, S.dzB));  // dz2
+    LK(mid_wgrad(c, S.a1, S.dzB, batch, nb));
     LK(launch_reduce_mid(S.partials, nb, S.grad + NET_W2, S.grad + NET_B2, c->st));
-    LK(launch_net_mid(1, S.dzB, m, batch, S.B2b, nullptr, S.z1, nullptr, S.dzA, c->st, S.lin));  // dz1
+    LK(mid_layer(c, 1, S.dzB, batch, S.B2b, nullptr, S.z1, nullptr, S.dzA));  // dz1
     LK(launch_net_in_wgrad<float>(S.ub, m, batch, S.shift, S.nub, S.dzA, S.partials, nb, c->st, S.lin));
     LK(launch_reduce_cols(S.partials, nb, NET_IN_PARTIAL, NET_IN_PARTIAL, S.grad + NET_W1, c->st));
     if (S.lin) {
@@ -312,6 +336,7 @@ extern "C" parareal_status parareal_coarse_model_grad(parareal_ctx *c, const flo
     CK(cudaMemcpyAsync(grad_out, S.grad, NET_PARAMS * 4, cudaMemcpyDeviceToDevice, c->st));
     CK(cudaMemcpyAsync(S.h_loss, S.loss_sum, sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
+    if ((s = net_check(c)) != PARAREAL_OK) return s;      // tensor-core completion waits
     if (loss) *loss = S.h_loss[0] / ((double)count * S.Pm);
     return PARAREAL_OK;
 }
@@ -370,6 +395,7 @@ extern "C" parareal_status parareal_train_coarse(parareal_ctx *c, const float *p
         }
         CK(cudaMemcpyAsync(S.h_loss, S.loss_sum, sizeof(double) * nbat, cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));
+        if ((s = net_check(c)) != PARAREAL_OK) return s;  // tensor-core completion waits
         double tot = 0.0;
         for (int bi = 0; bi < nbat; ++bi) tot += S.h_loss[bi];
         if (!std::isfinite(tot)) return fail(c, PARAREAL_E_DIVERGED, "training loss is not finite");

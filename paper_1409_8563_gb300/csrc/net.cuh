@@ -58,9 +58,15 @@ cudaError_t configure_net_tc();
 // `limit` tries on an mbarrier nothing arrives on; *flag = 1 when it gave up.
 cudaError_t launch_wait_selftest(long long limit, int *flag, cudaStream_t st);
 bool net_tc_supported(int m);
-cudaError_t launch_net_mid_tc(const __nv_bfloat16 *in, int m, int batch, const __nv_bfloat16 *Bt,
-                              const float *bias, __nv_bfloat16 *out, int lin, int *errflag,
-                              cudaStream_t st);
+// mode 0: forward (zout, if non-null, receives the FP32 pre-activations);
+// mode 1: input gradient through the mirrored operand Bt, times gelu'(zaux).
+cudaError_t launch_net_mid_tc(int mode, const __nv_bfloat16 *in, int m, int batch, const __nv_bfloat16 *Bt,
+                              const float *bias, const float *zaux, float *zout, __nv_bfloat16 *out,
+                              int lin, int *errflag, cudaStream_t st);
+// Weight gradient of a 16 -> 16 layer on the tensor cores: the same partials
+// as launch_net_mid_wgrad (nblocks slots of NET_MID_PARTIAL floats).
+cudaError_t launch_net_mid_wgrad_tc(const __nv_bfloat16 *x, const __nv_bfloat16 *dz, int m, int batch,
+                                    float *partials, int nblocks, int *errflag, cudaStream_t st);
 template <typename TU>
 cudaError_t launch_net_in_fwd(const TU *u, int m, const int s[3], const float *nu_hat, int batch,
                               const float *W1q, const float *b1, float *z1, __nv_bfloat16 *a1,
