@@ -584,7 +584,7 @@ def c4_learned_128(dev_index, steps=3, n_ics=63, epochs=10, batch=8, lr=1e-3, pi
             g_ms, _ = timed(lambda: c.propagate(1, src, dst, 1, 1), 10)
             out[name] = {"k_star": int(k), "time_to_1e-6_ms": ms, "g_apply_ms": g_ms,
                          "glups_in_solve": sum(N - j for j in range(k)) * n ** 3 * nf / ms / 1e6,
-                         "final_defect": float(h[-1, 2])}
+                         "final_defect": float(h[-1, 2]), "defects": [float(x) for x in h[:, 2]]}
             c.close()
     out["learned_over_stencil"] = out["learned"]["time_to_1e-6_ms"] / out["stencil"]["time_to_1e-6_ms"]
     out["learned_over_serial_fine"] = out["learned"]["time_to_1e-6_ms"] / out["serial_fine_ms"]
@@ -958,6 +958,42 @@ def batch64(correction="difference", queue=False, steps=1, warmup=1, dev_index=0
     return out
 
 
+def run_train_128(args):
+    """Training throughput of the learned propagator at 128^3 (batch 8 of
+    synthetic pairs, Adam): one warm-up epoch, then `steps` timed epochs of
+    8 batches; per batch: forward with pre-activations, loss, all gradients,
+    Adam and the operand copies.  The ncu target of the training kernels."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1409_8563_gb300 import configs, inputs, native
+    base, _ = configs.fp32_128()
+    n, N = base.n, base.n_slices
+    act = native.ACT_GELU if args.act == "gelu" else native.ACT_LINEAR
+    cfg = native.Config.make(n, N, base.T, base.dt_fine, base.dt_coarse, base.coarse_factor,
+                             fine_dtype=native.F32, coarse_kind=native.COARSE_LEARNED, nu0=base.nu0,
+                             nu_amp=base.nu_amp, nu_omega=base.nu_omega,
+                             learned_skip=native.SKIP_STENCIL, learned_act=act,
+                             correction_form=(native.CORRECTION_DIFFERENCE if act == native.ACT_LINEAR
+                                              else native.CORRECTION_STANDARD),
+                             learned_eval=native.EVAL_LAYERS)
+    ctx = native.Parareal(cfg)
+    npairs, batch = 64, 8
+    g = torch.Generator(device="cuda").manual_seed(0)
+    pu = torch.randn((npairs, n, n, n), device="cuda", generator=g)
+    pf = 0.9 * pu
+    sl = [i % N for i in range(npairs)]
+    ctx.set_coarse_model(inputs.initial_weights(seed=0))
+    ctx.train_coarse(pu, pf, sl, epochs=1, batch=batch, lr=1e-3, seed=1)
+    ms, _ = _timed(lambda: ctx.train_coarse(pu, pf, sl, epochs=args.steps, batch=batch, lr=1e-3, seed=2))
+    nb = args.steps * (npairs // batch)
+    print(json.dumps({"workload": f"train_128: learned propagator training at {n}^3, batch {batch}, "
+                                  f"{args.act} activations", "ms_per_batch": ms / nb,
+                      "points_per_s": batch * n ** 3 / (ms / nb / 1000.0), "batches": nb}))
+    ctx.close()
+    return 0
+
+
 def run_batch64(args):
     import __graft_entry__
     __graft_entry__.build()
@@ -1020,7 +1056,8 @@ def main():
                     help="skip the 128^3 learned-propagator comparison of the default line")
     ap.add_argument("--workload", default="fp32_256",
                     choices=["fp32_256", "fp32_128", "fp64_32", "learned_128", "learned_512",
-                             "learned_g", "batch64", "fine_sweep", "paper_faithful", "c4"])
+                             "learned_g", "batch64", "fine_sweep", "paper_faithful", "c4",
+                             "train_128"])
     ap.add_argument("--slices", type=int, default=8)
     ap.add_argument("--correction", default="difference", choices=["difference", "standard"],
                     help="evaluation of the Parareal correction (fp32_256 / fp32_128 / batch64)")
@@ -1038,6 +1075,8 @@ def main():
                     help="learned workloads: seeded training fields (default 63 at 128^3, 2 at 512^3)")
     ap.add_argument("--epochs", type=int, default=None, help="default 10 at 128^3, 16 at 512^3")
     ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--act", default="linear", choices=["linear", "gelu"],
+                    help="train_128: activations of the trained network")
     ap.add_argument("--lr", type=float, default=None, help="default 1e-3 at 128^3, 2e-3 at 512^3")
     args = ap.parse_args()
     big = args.workload == "learned_512"
@@ -1060,10 +1099,12 @@ def main():
         # the 128^3 learned-vs-stencil comparison of the headline line, alone
         import __graft_entry__
         __graft_entry__.build()
-        print(json.dumps(c4_learned_128(0, pipeline=args.pipeline)))
+        print(json.dumps(c4_learned_128(0, epochs=args.epochs, lr=args.lr, pipeline=args.pipeline)))
         return 0
     if args.workload == "fine_sweep":
         return run_fine_sweep(args)
+    if args.workload == "train_128":
+        return run_train_128(args)
     if args.workload == "paper_faithful":
         return run_paper_faithful(args)
     return run(args)

@@ -229,8 +229,8 @@ static parareal_status net_loss_grad(parareal_ctx *c, int batch, double *loss_sl
     LK(mid_layer(c, 0, S.a1, batch, S.B2f, b + NET_B2, nullptr, S.z2, S.a2));
     LK(mid_layer(c, 0, S.a2, batch, S.B3f, b + NET_B3, nullptr, S.z3, S.a3));
     const float gscale = (float)(2.0 / (double)F);
-    LK((launch_net_out_fwd<float, float>(S.a3, m, batch, S.W4q, b + NET_B4, S.ub, S.shift, nullptr,
-                                         S.fb, gscale, S.dz4, S.loss_parts, c->st, S.lin)));
+    LK(launch_net_out_mma_train(S.a3, m, batch, S.B4f, b + NET_B4, S.ub, S.shift, S.fb, gscale, S.dz4,
+                                S.loss_parts, c->st, S.lin));
     LK(launch_reduce_loss(S.loss_parts, tiles, loss_slot, c->st));
     // backward
     const int nb = net_partial_blocks(m, batch);

@@ -361,15 +361,20 @@ net_mid_wgrad(const bf16 *__restrict__ x, const bf16 *__restrict__ dz, int m, in
 
 // ---------------------------------------------------------------- layer 4
 
-// Inference form of the last layer on the tensor cores: the 16 -> 1
-// convolution as an implicit GEMM with N = 8 (output channel 0; B rows 1-7
-// are zero), the same tiling as net_mid, and the epilogue
-// g = S(u) + z4, z4 = acc + b4 (no bias in linear mode), written in TG.
+// The last layer on the tensor cores: the 16 -> 1 convolution as an implicit
+// GEMM with N = 8 (output channel 0; B rows 1-7 are zero), the same tiling as
+// net_mid, and the epilogue g = S(u) + z4, z4 = acc + b4 (no bias in linear
+// mode), written in TG if g_out is non-null.  With a target (training):
+// r = g - tgt, dz4 = bf16(r * grad_scale), and the block's sum of r^2 (fixed
+// order) into loss_partials[tile].
 template <typename TU, typename TG>
 __global__ void __launch_bounds__(256)
 net_out_mma(const bf16 *__restrict__ a3, int m, const bf16 *__restrict__ B4, const float *__restrict__ b4,
-            const TU *__restrict__ u, int sx, int sy, int sz, TG *__restrict__ g_out, int lin)
+            const TU *__restrict__ u, int sx, int sy, int sz, TG *__restrict__ g_out, int lin,
+            const float *__restrict__ tgt, float grad_scale, bf16 *__restrict__ dz4,
+            double *__restrict__ loss_partials)
 {
+    __shared__ double red[8];
     extern __shared__ uint4 sm_om[];
     uint4 *act = sm_om;                // 2000 chunks
     uint4 *bs = sm_om + 2000;          // 432 chunks: [27][8 n][2]
@@ -404,21 +409,39 @@ net_out_mma(const bf16 *__restrict__ a3, int m, const bf16 *__restrict__ B4, con
     }
     // output channel 0 sits in column 0 of the accumulator: lanes with tq == 0
     const int g = lane >> 2, tq = lane & 3;
-    if (tq != 0) return;
     const float bias = lin ? 0.f : b4[0];
+    double l = 0.0;
+    if (tq == 0) {
 #pragma unroll
-    for (int mt = 0; mt < 4; ++mt)
+        for (int mt = 0; mt < 4; ++mt)
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            const int row = g + 8 * hh;
-            const int x = row & 7, y = 2 * mt + (row >> 3), z = w;
-            const int gx = T.ox + x, gy = T.oy + y, gz = T.oz + z;
-            const long long p = ((long long)gz * m + gy) * m + gx;
-            const long long ps = ((long long)wrap(gz - sz + m, m) * m + wrap(gy - sy + m, m)) * m +
-                                 wrap(gx - sx + m, m);
-            const float z4 = acc[mt][2 * hh] + bias;
-            g_out[s * P + p] = (TG)((double)u[s * P + ps] + (double)z4);
+            for (int hh = 0; hh < 2; ++hh) {
+                const int row = g + 8 * hh;
+                const int x = row & 7, y = 2 * mt + (row >> 3), z = w;
+                const int gx = T.ox + x, gy = T.oy + y, gz = T.oz + z;
+                const long long p = ((long long)gz * m + gy) * m + gx;
+                const long long ps = ((long long)wrap(gz - sz + m, m) * m + wrap(gy - sy + m, m)) * m +
+                                     wrap(gx - sx + m, m);
+                const float z4 = acc[mt][2 * hh] + bias;
+                const double gv = (double)u[s * P + ps] + (double)z4;
+                if (g_out) g_out[s * P + p] = (TG)gv;
+                if (tgt) {
+                    const double rr = gv - (double)tgt[s * P + p];
+                    dz4[s * P + p] = __float2bfloat16_rn((float)rr * grad_scale);
+                    l += rr * rr;
+                }
+            }
+    }
+    if (tgt) {
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+        if (lane == 0) red[w] = l;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < 8; ++k) t += red[k];
+            loss_partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
         }
+    }
 }
 
 // g = S(u) + z4, z4 = conv(a3, W4) + b4.  With a target: r = g - tgt,
@@ -518,7 +541,14 @@ net_out_dgrad(const bf16 *__restrict__ dz4, int m, const float *__restrict__ W4q
 
 // dW4[ci][tap] = sum_p a3[p + tap][ci] dz4[p], db4 = sum_p dz4[p]; per-CTA
 // partials of NET_OUT_PARTIAL = 433 floats over a grid-stride set of tiles.
-__global__ void __launch_bounds__(448)
+// Work is split into warp-sized workers: worker j < 54 owns tap j >> 1 and
+// the eight channels of half j & 1 (one 16-byte chunk per point, eight FMAs
+// per shared-memory load), worker 54 the bias; warp w runs workers w, w + 16,
+// ... and its lanes take the tile's points lane, lane + 32, ... (consecutive
+// lanes read consecutive, swizzled chunks: no bank conflicts).  Lane partial
+// sums are folded by a fixed shuffle tree at the end.
+constexpr int OW_WARPS = 16, OW_WORKERS = 55, OW_PER_WARP = (OW_WORKERS + OW_WARPS - 1) / OW_WARPS;
+__global__ void __launch_bounds__(OW_WARPS * 32)
 net_out_wgrad(const bf16 *__restrict__ a3, const bf16 *__restrict__ dz4, int m, int tiles_total,
               float *__restrict__ partials)
 {
@@ -527,8 +557,12 @@ net_out_wgrad(const bf16 *__restrict__ a3, const bf16 *__restrict__ dz4, int m, 
     float *ds = reinterpret_cast<float *>(sm_ow + 2000);  // 512
     const long long P = (long long)m * m * m;
     const int tiles = (m >> 3) * (m >> 3) * (m >> 3);
-    const int ci = threadIdx.x / 27, t = threadIdx.x % 27;   // threads 0..431
-    float acc = 0.f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float acc[OW_PER_WARP][8];
+#pragma unroll
+    for (int k = 0; k < OW_PER_WARP; ++k)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[k][c] = 0.f;
     for (int tt = blockIdx.x; tt < tiles_total; tt += gridDim.x) {
         const int s = tt / tiles;
         const Tile T = tile_of(tt % tiles, m);
@@ -539,38 +573,71 @@ net_out_wgrad(const bf16 *__restrict__ a3, const bf16 *__restrict__ dz4, int m, 
             ds[i] = __bfloat162float(dz4[s * P + ((long long)(T.oz + lz) * m + (T.oy + ly)) * m + T.ox + lx]);
         }
         __syncthreads();
-        if (threadIdx.x < 432) {
-            const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-            const bf16 *a16 = reinterpret_cast<const bf16 *>(act);
-            for (int q = 0; q < 512; ++q) {
-                const int lx = q & 7, ly = (q >> 3) & 7, lz = q >> 6;
-                const int hq = ((lz + 1 + dz) * 10 + (ly + 1 + dy)) * 10 + lx + 1 + dx;
-                acc = fmaf(__bfloat162float(a16[chunk(hq, ci >> 3) * 8 + (ci & 7)]), ds[q], acc);
+#pragma unroll
+        for (int k = 0; k < OW_PER_WARP; ++k) {
+            const int j = warp + OW_WARPS * k;
+            if (j < 54) {
+                const int t = j >> 1, h = j & 1;
+                const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+                for (int i = 0; i < 16; ++i) {
+                    const int q = lane + 32 * i;
+                    const int lx = q & 7, ly = (q >> 3) & 7, lz = q >> 6;
+                    const int hq = ((lz + 1 + dz) * 10 + (ly + 1 + dy)) * 10 + lx + 1 + dx;
+                    const uint4 v = act[chunk(hq, h)];
+                    const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+                    const float d = ds[q];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) acc[k][c] = fmaf(__bfloat162float(e[c]), d, acc[k][c]);
+                }
+            } else if (j == 54) {
+                for (int i = 0; i < 16; ++i) acc[k][0] += ds[lane + 32 * i];
             }
-        } else if (threadIdx.x == 432) {
-            for (int q = 0; q < 512; ++q) acc += ds[q];
         }
     }
     float *out = partials + (long long)blockIdx.x * NET_OUT_PARTIAL;
-    if (threadIdx.x < 432) out[ci * 27 + t] = acc;
-    else if (threadIdx.x == 432) out[432] = acc;
+#pragma unroll
+    for (int k = 0; k < OW_PER_WARP; ++k) {
+        const int j = warp + OW_WARPS * k;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[k][c] += __shfl_xor_sync(0xffffffffu, acc[k][c], o);
+        if (lane == 0) {
+            if (j < 54) {
+                const int t = j >> 1, h = j & 1;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) out[(8 * h + c) * 27 + t] = acc[k][c];
+            } else if (j == 54) {
+                out[432] = acc[k][0];
+            }
+        }
+    }
 }
 
 // dW1[co][0][tap] = sum_p x0[p + tap] dz1[p][co]   (x0 = bf16(S(u)))
 // dW1[co][1][tap] = sum_samples bf16(nu_hat_s) sum_p dz1[p][co],  db1[co] = sum_p dz1[p][co]
 // (linear mode: dW1[co][1][tap] = sum_samples bf16(nu_hat_s) sum_p x0[p + tap] dz1[p][co])
 // partial layout: [16][2][27] then [16] (NET_IN_PARTIAL = 880 floats).
+// Warp-sized workers as in net_out_wgrad: worker j < 54 owns tap j >> 1 and
+// output channels 8 (j & 1) .. + 7 (one chunk of dz1 per point, eight FMAs
+// per pair of loads), workers 54 and 55 the channel sums of each half; the
+// per-tile lane sums are weighted by the tile's sample's nu_hat for channel 2.
+constexpr int IW_WARPS = 16, IW_WORKERS = 56, IW_PER_WARP = (IW_WORKERS + IW_WARPS - 1) / IW_WARPS;
 template <typename TU>
-__global__ void __launch_bounds__(448)
+__global__ void __launch_bounds__(IW_WARPS * 32)
 net_in_wgrad(const TU *__restrict__ u, int m, int sx, int sy, int sz, const float *__restrict__ nu_hat,
              const bf16 *__restrict__ dz1, int tiles_total, float *__restrict__ partials, int lin)
 {
     __shared__ float xs[1000];
-    __shared__ float ds[512 * 17];    // [point][16] padded to 17
+    __shared__ uint4 dzs[1024];        // dz1 of the tile's 512 points, swizzled chunks
     const long long P = (long long)m * m * m;
     const int tiles = (m >> 3) * (m >> 3) * (m >> 3);
-    const int co = threadIdx.x / 27, t = threadIdx.x % 27;
-    float acc = 0.f, accb = 0.f, accnu = 0.f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float acc[IW_PER_WARP][8], accnu[IW_PER_WARP][8];
+#pragma unroll
+    for (int k = 0; k < IW_PER_WARP; ++k)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[k][c] = accnu[k][c] = 0.f;
     for (int tt = blockIdx.x; tt < tiles_total; tt += gridDim.x) {
         const int s = tt / tiles;
         const Tile T = tile_of(tt % tiles, m);
@@ -582,39 +649,82 @@ net_in_wgrad(const TU *__restrict__ u, int m, int sx, int sy, int sz, const floa
             const int gz = wrap(wrap(T.oz + hz - 1, m) - sz + m, m);
             xs[i] = bf16r((float)u[s * P + ((long long)gz * m + gy) * m + gx]);
         }
-        for (int i = threadIdx.x; i < 512 * 16; i += blockDim.x) {
-            const int q = i >> 4, c = i & 15;
+        const uint4 *dsrc = reinterpret_cast<const uint4 *>(dz1);
+        for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+            const int q = i >> 1, h = i & 1;
             const int lx = q & 7, ly = (q >> 3) & 7, lz = q >> 6;
             const long long p = s * P + ((long long)(T.oz + lz) * m + (T.oy + ly)) * m + T.ox + lx;
-            ds[q * 17 + c] = __bfloat162float(dz1[16 * p + c]);
+            dzs[chunk(q, h)] = dsrc[2 * p + h];
         }
         __syncthreads();
-        if (threadIdx.x < 432) {
-            const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-            float part = 0.f;
-            for (int q = 0; q < 512; ++q) {
-                const int lx = q & 7, ly = (q >> 3) & 7, lz = q >> 6;
-                part = fmaf(xs[((lz + 1 + dz) * 10 + (ly + 1 + dy)) * 10 + lx + 1 + dx], ds[q * 17 + co], part);
+        const float nus = bf16r(nu_hat[s]);
+#pragma unroll
+        for (int k = 0; k < IW_PER_WARP; ++k) {
+            const int j = warp + IW_WARPS * k;
+            if (j >= IW_WORKERS) continue;
+            const int h = j & 1;
+            float part[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) part[c] = 0.f;
+            if (j < 54) {
+                const int t = j >> 1;
+                const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+                for (int i = 0; i < 16; ++i) {
+                    const int q = lane + 32 * i;
+                    const int lx = q & 7, ly = (q >> 3) & 7, lz = q >> 6;
+                    const float x = xs[((lz + 1 + dz) * 10 + (ly + 1 + dy)) * 10 + lx + 1 + dx];
+                    const uint4 v = dzs[chunk(q, h)];
+                    const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) part[c] = fmaf(x, __bfloat162float(e[c]), part[c]);
+                }
+                if (lin) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) accnu[k][c] = fmaf(nus, part[c], accnu[k][c]);
+                }
+            } else {
+                for (int i = 0; i < 16; ++i) {
+                    const uint4 v = dzs[chunk(lane + 32 * i, h)];
+                    const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) part[c] += __bfloat162float(e[c]);
+                }
+#pragma unroll
+                for (int c = 0; c < 8; ++c) accnu[k][c] = fmaf(nus, part[c], accnu[k][c]);
             }
-            acc += part;
-            if (lin) accnu = fmaf(bf16r(nu_hat[s]), part, accnu);
-        } else if (threadIdx.x < 448) {
-            const int c = threadIdx.x - 432;
-            float sum = 0.f;
-            for (int q = 0; q < 512; ++q) sum += ds[q * 17 + c];
-            accb += sum;
-            accnu = fmaf(bf16r(nu_hat[s]), sum, accnu);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[k][c] += part[c];
         }
     }
     float *out = partials + (long long)blockIdx.x * NET_IN_PARTIAL;
-    if (threadIdx.x < 432) {
-        out[co * 54 + t] = acc;
-        if (lin) out[co * 54 + 27 + t] = accnu;
-    } else if (threadIdx.x < 448) {
-        const int c = threadIdx.x - 432;
-        if (!lin)
-            for (int k = 0; k < 27; ++k) out[c * 54 + 27 + k] = accnu;
-        out[864 + c] = accb;
+#pragma unroll
+    for (int k = 0; k < IW_PER_WARP; ++k) {
+        const int j = warp + IW_WARPS * k;
+        if (j >= IW_WORKERS) continue;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                acc[k][c] += __shfl_xor_sync(0xffffffffu, acc[k][c], o);
+                accnu[k][c] += __shfl_xor_sync(0xffffffffu, accnu[k][c], o);
+            }
+        if (lane != 0) continue;
+        const int h = j & 1;
+        if (j < 54) {
+            const int t = j >> 1;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                out[(8 * h + c) * 54 + t] = acc[k][c];
+                if (lin) out[(8 * h + c) * 54 + 27 + t] = accnu[k][c];
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                if (!lin)
+                    for (int q = 0; q < 27; ++q) out[(8 * h + c) * 54 + 27 + q] = accnu[k][c];
+                out[864 + 8 * h + c] = acc[k][c];
+            }
+        }
     }
 }
 
@@ -629,13 +739,21 @@ __global__ void reduce_cols(const float *__restrict__ partials, int nb, int stri
     out[j] = (float)s;
 }
 
-__global__ void reduce_loss(const double *__restrict__ parts, int nb, double *__restrict__ out)
+// out[0] = sum of parts[0 .. nb): one block; thread i sums i, i + 1024, ...,
+// then a fixed tree folds the 1024 sums (the same order on every call).
+__global__ void __launch_bounds__(1024)
+reduce_loss(const double *__restrict__ parts, int nb, double *__restrict__ out)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int b = 0; b < nb; ++b) s += parts[b];
-        out[0] = s;
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 1024) s += parts[b];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) out[0] = red[0];
 }
 
 // Adam (Kingma & Ba 2015) on FP32 masters with bias correction.
@@ -776,7 +894,7 @@ cudaError_t launch_net_out_dgrad(const bf16 *dz4, int m, int batch, const float 
 cudaError_t launch_net_out_wgrad(const bf16 *a3, const bf16 *dz4, int m, int batch, float *partials,
                                  int nblocks, cudaStream_t st)
 {
-    net_out_wgrad<<<nblocks, 448, OW_SMEM, st>>>(a3, dz4, m, (int)tiles_of(m) * batch, partials);
+    net_out_wgrad<<<nblocks, OW_WARPS * 32, OW_SMEM, st>>>(a3, dz4, m, (int)tiles_of(m) * batch, partials);
     return cudaGetLastError();
 }
 
@@ -784,7 +902,7 @@ template <typename TU>
 cudaError_t launch_net_in_wgrad(const TU *u, int m, int batch, const int s[3], const float *nu_hat,
                                 const bf16 *dz1, float *partials, int nblocks, cudaStream_t st, int lin)
 {
-    net_in_wgrad<TU><<<nblocks, 448, 0, st>>>(u, m, s[0], s[1], s[2], nu_hat, dz1,
+    net_in_wgrad<TU><<<nblocks, IW_WARPS * 32, 0, st>>>(u, m, s[0], s[1], s[2], nu_hat, dz1,
                                               (int)tiles_of(m) * batch, partials, lin);
     return cudaGetLastError();
 }
@@ -801,7 +919,7 @@ cudaError_t launch_reduce_cols(const float *partials, int nb, int stride, int L,
 
 cudaError_t launch_reduce_loss(const double *parts, int nb, double *out, cudaStream_t st)
 {
-    reduce_loss<<<1, 32, 0, st>>>(parts, nb, out);
+    reduce_loss<<<1, 1024, 0, st>>>(parts, nb, out);
     return cudaGetLastError();
 }
 
@@ -826,7 +944,17 @@ cudaError_t launch_net_out_mma(const bf16 *a3, int m, int batch, const bf16 *B4f
                                const TU *u, const int s[3], TG *g_out, cudaStream_t st, int lin)
 {
     net_out_mma<TU, TG><<<dim3(tiles_of(m), batch), 256, OM_SMEM, st>>>(a3, m, B4f, b4, u, s[0], s[1],
-                                                                       s[2], g_out, lin);
+                                                                       s[2], g_out, lin, nullptr, 0.f,
+                                                                       nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_net_out_mma_train(const bf16 *a3, int m, int batch, const bf16 *B4f, const float *b4,
+                                     const float *u, const int s[3], const float *tgt, float grad_scale,
+                                     bf16 *dz4, double *loss_partials, cudaStream_t st, int lin)
+{
+    net_out_mma<float, float><<<dim3(tiles_of(m), batch), 256, OM_SMEM, st>>>(
+        a3, m, B4f, b4, u, s[0], s[1], s[2], nullptr, lin, tgt, grad_scale, dz4, loss_partials);
     return cudaGetLastError();
 }
 template cudaError_t launch_net_out_mma<float, float>(const bf16 *, int, int, const bf16 *, const float *,

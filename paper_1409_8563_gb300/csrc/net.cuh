@@ -99,6 +99,12 @@ cudaError_t launch_adam(float *p, const float *g, float *mo, float *vo, int L, f
 cudaError_t launch_prepare_operands(const float *master, float *W1q, __nv_bfloat16 *B2f,
                                     __nv_bfloat16 *B3f, __nv_bfloat16 *B2b, __nv_bfloat16 *B3b,
                                     float *W4q, __nv_bfloat16 *B4f, cudaStream_t st);
+// Last layer of training on the tensor cores: loss terms and dz4 against the
+// target, as launch_net_out_fwd with a target, no G output.
+cudaError_t launch_net_out_mma_train(const __nv_bfloat16 *a3, int m, int batch, const __nv_bfloat16 *B4f,
+                                     const float *b4, const float *u, const int s[3], const float *tgt,
+                                     float grad_scale, __nv_bfloat16 *dz4, double *loss_partials,
+                                     cudaStream_t st, int lin = 0);
 // Last layer for inference on the tensor cores (B4f: [27][8][16], row 0 = W4).
 template <typename TU, typename TG>
 cudaError_t launch_net_out_mma(const __nv_bfloat16 *a3, int m, int batch, const __nv_bfloat16 *B4f,

@@ -337,7 +337,7 @@ constexpr int DZ_CHUNKS = ZB * 16 * 2 * 8;        // dz tile: 8 x 16 x ZB points
 // two CTAs (2 x 256 tensor-memory columns) share an SM
 constexpr int WG_SLACK = 2368;
 constexpr uint32_t WG_TMEM_COLS = 256;            // 9 accumulators of 16 columns
-constexpr size_t WG_SMEM = (size_t)(2 * HALO_ALLOC + 2 * DZ_CHUNKS + WG_SLACK) * 16 + 2 * 128 * 4;
+constexpr size_t WG_SMEM = (size_t)(2 * HALO_ALLOC + 2 * DZ_CHUNKS + WG_SLACK) * 16 + 128 * 16 * 4;
 
 // dz tile of T: chunk(z, y, h, x) = ((z * 16 + y) * 2 + h) * 8 + x
 __device__ __forceinline__ void dz_async(uint32_t buf, const bf16 *__restrict__ dz, const TileTC &T, int m,
@@ -396,8 +396,9 @@ net_mid_wgrad_tc(const bf16 *__restrict__ x, const bf16 *__restrict__ dz, int m,
     // MN-major A and B (transpose bits 15 and 16 of the instruction descriptor)
     constexpr uint32_t IDESC = idesc_bf16(128, 16) | (1u << 15) | (1u << 16);
 
-    const int bco = tid & 15;                       // bias-gradient channel of this thread
-    float dbias = 0.f;
+    float dbias[16];                                // bias-gradient sums of this thread's points
+#pragma unroll
+    for (int c = 0; c < 16; ++c) dbias[c] = 0.f;
     uint32_t parity = 0;
     int buf = 0, ntile = 0;
     bool failed = false;
@@ -444,13 +445,22 @@ net_mid_wgrad_tc(const bf16 *__restrict__ x, const bf16 *__restrict__ dz, int m,
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
                          ::"r"(mbar_a) : "memory");
         }
-        // bias gradient on the CUDA cores: thread tid sums channel tid & 15 over
-        // the tile points tid >> 4, + 8, ...
+        // bias gradient on the CUDA cores: thread tid sums all 16 channels of
+        // the tile points tid and tid + 128 (two 16-byte loads each; the 8
+        // lanes of a quarter warp read 8 consecutive chunks)
         {
-            const bf16 *d16 = reinterpret_cast<const bf16 *>(dz0 + buf * DZ_CHUNKS);
-            for (int q = tid >> 4; q < 8 * 16 * ZB; q += TC_THREADS / 16) {
+            const uint4 *dt = dz0 + buf * DZ_CHUNKS;
+#pragma unroll
+            for (int k = 0; k < 8 * 16 * ZB / TC_THREADS; ++k) {
+                const int q = tid + TC_THREADS * k;
                 const int xq = q & 7, yq = (q >> 3) & 15, zq = q >> 7;
-                dbias += __bfloat162float(d16[((((zq * 16 + yq) * 2 + (bco >> 3)) * 8 + xq) * 8) + (bco & 7)]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint4 v = dt[((zq * 16 + yq) * 2 + h) * 8 + xq];
+                    const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) dbias[8 * h + c] += __bfloat162float(e[c]);
+                }
             }
         }
     }
@@ -488,12 +498,13 @@ net_mid_wgrad_tc(const bf16 *__restrict__ x, const bf16 *__restrict__ dz, int m,
             }
         }
     }
-    // bias gradient: the 8 threads of each channel, fixed order
-    red[tid] = dbias;
+    // bias gradient: the threads' sums in a fixed order
+#pragma unroll
+    for (int c = 0; c < 16; ++c) red[tid * 16 + c] = dbias[c];
     __syncthreads();
     if (tid < 16) {
         float sacc = 0.f;
-        for (int k = 0; k < TC_THREADS / 16; ++k) sacc += red[k * 16 + tid];
+        for (int k = 0; k < TC_THREADS; ++k) sacc += red[k * 16 + tid];
         out[27 * 256 + tid] = sacc;
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
