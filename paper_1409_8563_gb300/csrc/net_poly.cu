@@ -149,21 +149,24 @@ poly_prolong_kernel(const T *__restrict__ cnew, const T *__restrict__ cold, cons
 
 // The same sum for TT taps per axis known at compile time (r = 4: 4, r = 8:
 // 3), with a thread's phase kernel in registers: thread t takes phase
-// t % min(r^3, 256) and every (256 / min(r^3, 256))-th coarse cell of the
-// brick, so the 32 lanes of a warp are 32 phases of one coarse cell and
-// read at most 2^3 distinct window entries per tap.  The taps are summed in
-// the order of the generic kernel, so both give the same value.
-template <typename T, int TT>
+// t % min(r^3, 256) and whole x-rows of the brick's CB coarse cells (rows
+// t / min(r^3, 256), + 256 / min(r^3, 256), ...), so the 32 lanes of a warp
+// are 32 phases of the same cells and read at most 2^3 distinct window
+// entries per load.  The CB cells of a row share their window: per (tz, ty)
+// a thread loads CB + TT - 1 entries for CB x TT FMAs.  Each cell's taps are
+// summed in the order of the generic kernel, so both give the same value.
+template <typename T, int TT, int CB>
 __global__ void __launch_bounds__(PP_THREADS)
 poly_prolong_reg_kernel(const T *__restrict__ cnew, const T *__restrict__ cold, const float *__restrict__ W,
                         int n, int r, int lo_off, int win, T *__restrict__ out)
 {
     constexpr int T3 = TT * TT * TT;
+    constexpr int RW = CB + TT - 1;                  // window entries of one row of cells
     extern __shared__ __align__(16) unsigned char pp_smem[];
     T *dcw = reinterpret_cast<T *>(pp_smem);
-    const int R3 = r * r * r, nc = n / r, nb = n / PP_B, cb = PP_B / r, cb3 = cb * cb * cb;
+    const int R3 = r * r * r, nc = n / r, nb = n / PP_B;
     const int bx = blockIdx.x % nb, by = (blockIdx.x / nb) % nb, bz = blockIdx.x / (nb * nb);
-    const int cx0 = bx * cb + lo_off, cy0 = by * cb + lo_off, cz0 = bz * cb + lo_off;
+    const int cx0 = bx * CB + lo_off, cy0 = by * CB + lo_off, cz0 = bz * CB + lo_off;
     auto wrap = [nc](int v) { v %= nc; return v < 0 ? v + nc : v; };
     const int w3 = win * win * win;
     for (int i = threadIdx.x; i < w3; i += blockDim.x) {
@@ -181,20 +184,29 @@ poly_prolong_reg_kernel(const T *__restrict__ cnew, const T *__restrict__ cold, 
         for (int k = 0; k < T3; ++k) w[k] = (T)W[rho * (T3 + 1) + k];
         const int sx = phase_start(rx, r) - lo_off, sy = phase_start(ry, r) - lo_off,
                   sz = phase_start(rz, r) - lo_off;
-        for (int cell = g; cell < cb3; cell += per) {
-            const int cx = cell % cb, cy = (cell / cb) % cb, cz = cell / (cb * cb);
-            const T *d0 = dcw + ((cz + sz) * win + (cy + sy)) * win + cx + sx;
-            T acc = (T)0;
+        for (int row = g; row < CB * CB; row += per) {
+            const int cy = row % CB, cz = row / CB;
+            const T *d0 = dcw + ((cz + sz) * win + (cy + sy)) * win + sx;
+            T acc[CB];
+#pragma unroll
+            for (int c = 0; c < CB; ++c) acc[c] = (T)0;
 #pragma unroll
             for (int tz = 0; tz < TT; ++tz)
 #pragma unroll
-                for (int ty = 0; ty < TT; ++ty)
+                for (int ty = 0; ty < TT; ++ty) {
+                    T v[RW];
+#pragma unroll
+                    for (int e = 0; e < RW; ++e) v[e] = d0[(tz * win + ty) * win + e];
 #pragma unroll
                     for (int tx = 0; tx < TT; ++tx)
-                        acc = fma(w[(tz * TT + ty) * TT + tx], d0[(tz * win + ty) * win + tx], acc);
-            const long long gx = (long long)bx * PP_B + cx * r + rx, gy = (long long)by * PP_B + cy * r + ry,
-                            gz = (long long)bz * PP_B + cz * r + rz;
-            out[(gz * n + gy) * n + gx] = acc;
+#pragma unroll
+                        for (int c = 0; c < CB; ++c)
+                            acc[c] = fma(w[(tz * TT + ty) * TT + tx], v[c + tx], acc[c]);
+                }
+            const long long gy = (long long)by * PP_B + cy * r + ry, gz = (long long)bz * PP_B + cz * r + rz;
+#pragma unroll
+            for (int c = 0; c < CB; ++c)
+                out[(gz * n + gy) * n + (long long)bx * PP_B + c * r + rx] = acc[c];
         }
     }
 }
@@ -249,12 +261,12 @@ cudaError_t configure_poly_kernels(int r)
     return e;
 }
 
-template <typename T, int TT>
+template <typename T, int TT, int CB>
 static void launch_reg(const T *cnew, const T *cold, const float *W, int n, int r, int lo, int win, T *out,
                        cudaStream_t st)
 {
     const int nb = n / PP_B;
-    poly_prolong_reg_kernel<T, TT><<<nb * nb * nb, PP_THREADS, (size_t)win * win * win * sizeof(T), st>>>(
+    poly_prolong_reg_kernel<T, TT, CB><<<nb * nb * nb, PP_THREADS, (size_t)win * win * win * sizeof(T), st>>>(
         cnew, cold, W, n, r, lo, win, out);
 }
 
@@ -276,10 +288,10 @@ cudaError_t launch_poly_prolong(const T *cnew, const T *cold, const float *W, in
     if (n % PP_B || PP_B % r) return cudaErrorInvalidValue;
     int TT, lo, win;
     poly_geometry(r, &TT, &lo, &win);
-    if (TT == 4) {
-        launch_reg<T, 4>(cnew, cold, W, n, r, lo, win, out, st);
-    } else if (TT == 3) {
-        launch_reg<T, 3>(cnew, cold, W, n, r, lo, win, out, st);
+    if (TT == 4 && r == 4) {
+        launch_reg<T, 4, PP_B / 4>(cnew, cold, W, n, r, lo, win, out, st);
+    } else if (TT == 3 && r == 8) {
+        launch_reg<T, 3, PP_B / 8>(cnew, cold, W, n, r, lo, win, out, st);
     } else {
         const int nb = n / PP_B;
         poly_prolong_kernel<T><<<nb * nb * nb, PP_THREADS, poly_smem_bytes(r, sizeof(T)), st>>>(
