@@ -444,58 +444,6 @@ net_out_mma(const bf16 *__restrict__ a3, int m, const bf16 *__restrict__ B4, con
     }
 }
 
-// g = S(u) + z4, z4 = conv(a3, W4) + b4.  With a target: r = g - tgt,
-// dz4 = bf16(r * grad_scale), loss partial sum r^2 per block.
-template <typename TU, typename TG>
-__global__ void __launch_bounds__(512)
-net_out_fwd(const bf16 *__restrict__ a3, int m, const float *__restrict__ W4q, const float *__restrict__ b4,
-            const TU *__restrict__ u, int sx, int sy, int sz, TG *__restrict__ g_out,
-            const float *__restrict__ tgt, float grad_scale, bf16 *__restrict__ dz4,
-            double *__restrict__ loss_partials, int lin)
-{
-    extern __shared__ uint4 sm_out[];
-    uint4 *act = sm_out;                                    // 2000 chunks
-    float *w = reinterpret_cast<float *>(sm_out + 2000);    // [16][27]
-    __shared__ double red[16];
-    const int s = blockIdx.y;
-    const long long P = (long long)m * m * m;
-    const Tile T = tile_of(blockIdx.x, m);
-    load_halo16(act, a3 + 16 * s * P, T, m);
-    for (int i = threadIdx.x; i < 432; i += blockDim.x) w[i] = W4q[i];
-    __syncthreads();
-    const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;
-    float acc = lin ? 0.f : b4[0];
-    for (int t = 0; t < 27; ++t) {
-        const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-        const int q = ((lz + 1 + dz) * 10 + (ly + 1 + dy)) * 10 + lx + 1 + dx;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint4 v = act[chunk(q, h)];
-            const bf16 *e = reinterpret_cast<const bf16 *>(&v);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) acc = fmaf(w[(8 * h + c) * 27 + t], __bfloat162float(e[c]), acc);
-        }
-    }
-    const int gx = T.ox + lx, gy = T.oy + ly, gz = T.oz + lz;
-    const long long p = ((long long)gz * m + gy) * m + gx;
-    const long long ps = ((long long)wrap(gz - sz + m, m) * m + wrap(gy - sy + m, m)) * m + wrap(gx - sx + m, m);
-    const double g = (double)u[s * P + ps] + (double)acc;
-    if (g_out) g_out[s * P + p] = (TG)g;
-    if (tgt) {
-        const double rr = g - (double)tgt[s * P + p];
-        dz4[s * P + p] = __float2bfloat16_rn((float)rr * grad_scale);
-        double l = rr * rr;
-        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int k = 0; k < 16; ++k) t += red[k];
-            loss_partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
-        }
-    }
-}
-
 // dz3[p][ci] = bf16( (sum_tap dz4[p - tap] W4[ci][tap]) * gelu'(z3[p][ci]) )
 __global__ void __launch_bounds__(512)
 net_out_dgrad(const bf16 *__restrict__ dz4, int m, const float *__restrict__ W4q,
@@ -821,7 +769,6 @@ template cudaError_t launch_net_in_fwd<double>(const double *, int, const int *,
 
 static constexpr size_t MID_SMEM = (2000 + 864) * 16;
 static constexpr size_t WG_SMEM = (2000 + 1024) * 16;
-static constexpr size_t OUT_SMEM = 2000 * 16 + 432 * 4;
 static constexpr size_t OW_SMEM = 2000 * 16 + 512 * 4;
 
 cudaError_t configure_net_kernels()
@@ -830,10 +777,6 @@ cudaError_t configure_net_kernels()
     if ((e = cudaFuncSetAttribute(net_mid<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MID_SMEM))) return e;
     if ((e = cudaFuncSetAttribute(net_mid<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MID_SMEM))) return e;
     if ((e = cudaFuncSetAttribute(net_mid_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WG_SMEM))) return e;
-    if ((e = cudaFuncSetAttribute(net_out_fwd<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OUT_SMEM))) return e;
-    if ((e = cudaFuncSetAttribute(net_out_fwd<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OUT_SMEM))) return e;
-    if ((e = cudaFuncSetAttribute(net_out_fwd<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OUT_SMEM))) return e;
-    if ((e = cudaFuncSetAttribute(net_out_fwd<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OUT_SMEM))) return e;
     if ((e = cudaFuncSetAttribute(net_out_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OW_SMEM))) return e;
     return cudaSuccess;
 }
@@ -861,28 +804,6 @@ cudaError_t launch_net_mid_wgrad(const bf16 *x, const bf16 *dz, int m, int batch
     net_mid_wgrad<<<nblocks, 256, WG_SMEM, st>>>(x, dz, m, (int)tiles_of(m) * batch, partials);
     return cudaGetLastError();
 }
-
-template <typename TU, typename TG>
-cudaError_t launch_net_out_fwd(const bf16 *a3, int m, int batch, const float *W4q, const float *b4,
-                               const TU *u, const int s[3], TG *g_out, const float *tgt, float grad_scale,
-                               bf16 *dz4, double *loss_partials, cudaStream_t st, int lin)
-{
-    net_out_fwd<TU, TG><<<dim3(tiles_of(m), batch), 512, OUT_SMEM, st>>>(
-        a3, m, W4q, b4, u, s[0], s[1], s[2], g_out, tgt, grad_scale, dz4, loss_partials, lin);
-    return cudaGetLastError();
-}
-template cudaError_t launch_net_out_fwd<float, float>(const bf16 *, int, int, const float *, const float *,
-                                                      const float *, const int *, float *, const float *,
-                                                      float, bf16 *, double *, cudaStream_t, int);
-template cudaError_t launch_net_out_fwd<double, double>(const bf16 *, int, int, const float *, const float *,
-                                                        const double *, const int *, double *, const float *,
-                                                        float, bf16 *, double *, cudaStream_t, int);
-template cudaError_t launch_net_out_fwd<float, double>(const bf16 *, int, int, const float *, const float *,
-                                                       const float *, const int *, double *, const float *,
-                                                       float, bf16 *, double *, cudaStream_t, int);
-template cudaError_t launch_net_out_fwd<double, float>(const bf16 *, int, int, const float *, const float *,
-                                                       const double *, const int *, float *, const float *,
-                                                       float, bf16 *, double *, cudaStream_t, int);
 
 cudaError_t launch_net_out_dgrad(const bf16 *dz4, int m, int batch, const float *W4q, const float *z3,
                                  bf16 *dz3, cudaStream_t st, int lin)

@@ -77,11 +77,6 @@ cudaError_t launch_net_mid(int mode, const __nv_bfloat16 *in, int m, int batch,
 int net_partial_blocks(int m, int batch);
 cudaError_t launch_net_mid_wgrad(const __nv_bfloat16 *x, const __nv_bfloat16 *dz, int m, int batch,
                                  float *partials, int nblocks, cudaStream_t st);
-template <typename TU, typename TG>
-cudaError_t launch_net_out_fwd(const __nv_bfloat16 *a3, int m, int batch, const float *W4q,
-                               const float *b4, const TU *u, const int s[3], TG *g_out,
-                               const float *tgt, float grad_scale, __nv_bfloat16 *dz4,
-                               double *loss_partials, cudaStream_t st, int lin = 0);
 cudaError_t launch_net_out_dgrad(const __nv_bfloat16 *dz4, int m, int batch, const float *W4q,
                                  const float *z3, __nv_bfloat16 *dz3, cudaStream_t st, int lin = 0);
 cudaError_t launch_net_out_wgrad(const __nv_bfloat16 *a3, const __nv_bfloat16 *dz4, int m, int batch,
@@ -99,8 +94,9 @@ cudaError_t launch_adam(float *p, const float *g, float *mo, float *vo, int L, f
 cudaError_t launch_prepare_operands(const float *master, float *W1q, __nv_bfloat16 *B2f,
                                     __nv_bfloat16 *B3f, __nv_bfloat16 *B2b, __nv_bfloat16 *B3b,
                                     float *W4q, __nv_bfloat16 *B4f, cudaStream_t st);
-// Last layer of training on the tensor cores: loss terms and dz4 against the
-// target, as launch_net_out_fwd with a target, no G output.
+// Last layer of training on the tensor cores: g = S(u) + z4 against the
+// target, dz4 = bf16((g - tgt) * grad_scale) and the per-tile sums of
+// (g - tgt)^2 in loss_partials (no G output).
 cudaError_t launch_net_out_mma_train(const __nv_bfloat16 *a3, int m, int batch, const __nv_bfloat16 *B4f,
                                      const float *b4, const float *u, const int s[3], const float *tgt,
                                      float grad_scale, __nv_bfloat16 *dz4, double *loss_partials,
