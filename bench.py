@@ -796,13 +796,14 @@ def run_learned_128(args):
 
 def run_learned_512(args):
     """512^3, N = 16 (dt_F = 1/32768, stencil G on 64^3 at 1/512): Parareal with
-    the linear learned propagator (stencil skip, composed evaluation,
-    difference-form correction), trained here on the pairs the fine solver
-    generates from --n-ics seeded fields (16 pairs each), against
+    the linear learned propagator (stencil skip, phase kernels on the coarse
+    grid, difference-form correction), trained here on the pairs the fine
+    solver generates from --n-ics seeded fields (16 pairs each), against
     stencil-G Parareal and the serial fine run: iterations and time to
-    d^k <= 1e-6, fine GLUP/s inside each solve.  One solve each (a solve
-    takes minutes at this size); contexts are built one after another to
-    bound the device memory (~160 GB at the peak, during training)."""
+    d^k <= 1e-6, fine GLUP/s inside each solve, clocks sampled over the
+    solves.  One solve each (a solve takes about a minute at this size);
+    contexts are built one after another to bound the device memory
+    (~160 GB at the peak, during training)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -844,28 +845,30 @@ def run_learned_512(args):
     u = torch.from_numpy(u0).cuda()
     ref = torch.empty((n,) * 3, dtype=torch.float64, device="cuda")
     runs = {}
-    for name, kind in (("stencil_difference_form", native.COARSE_STENCIL),
-                       ("learned_linear_polyphase", native.COARSE_LEARNED)):
-        # the trained linear net folded with the prolongation into phase kernels
-        c = native.Parareal(mk(kind, native.EVAL_POLYPHASE if kind == native.COARSE_LEARNED
-                               else native.EVAL_LAYERS))
-        c.autotune(TUNE_CACHE)
-        if kind == native.COARSE_LEARNED:
-            c.set_coarse_model(w)
-        c.set_problem(u)
-        if "serial_fine_ms" not in out:
-            ms, _ = _timed(lambda: c.serial_fine(ref, as_reference=True))
-            out["serial_fine_ms"] = ms
-            out["serial_fine_glups"] = P * N * nf / ms / 1e6
-        else:
-            c.set_reference(ref)
-        ms, (k, h) = _timed(lambda: c.iterate(N, TOL, native.STOP_DEFECT))
-        ups = sum(N - j for j in range(k)) * P * nf
-        runs[name] = {"k_star": k, "time_to_1e-6_ms": ms, "glups_in_solve": ups / ms / 1e6,
-                      "defects": [float(x) for x in h[:, 2]],
-                      "launch_shape_fine": list(c.launch_shape()[0])}
-        c.close()
+    with ClockSampler(0) as clk:
+        for name, kind in (("stencil_difference_form", native.COARSE_STENCIL),
+                           ("learned_linear_polyphase", native.COARSE_LEARNED)):
+            # the trained linear net folded with the prolongation into phase kernels
+            c = native.Parareal(mk(kind, native.EVAL_POLYPHASE if kind == native.COARSE_LEARNED
+                                   else native.EVAL_LAYERS))
+            c.autotune(TUNE_CACHE)
+            if kind == native.COARSE_LEARNED:
+                c.set_coarse_model(w)
+            c.set_problem(u)
+            if "serial_fine_ms" not in out:
+                ms, _ = _timed(lambda: c.serial_fine(ref, as_reference=True))
+                out["serial_fine_ms"] = ms
+                out["serial_fine_glups"] = P * N * nf / ms / 1e6
+            else:
+                c.set_reference(ref)
+            ms, (k, h) = _timed(lambda: c.iterate(N, TOL, native.STOP_DEFECT))
+            ups = sum(N - j for j in range(k)) * P * nf
+            runs[name] = {"k_star": k, "time_to_1e-6_ms": ms, "glups_in_solve": ups / ms / 1e6,
+                          "defects": [float(x) for x in h[:, 2]],
+                          "launch_shape_fine": list(c.launch_shape()[0])}
+            c.close()
     out["runs"] = runs
+    out["clocks"] = clk.summary()
     print(json.dumps(out))
     return 0
 
