@@ -327,14 +327,19 @@ parareal_status parareal_make_pairs(parareal_ctx *ctx, const float *ics, int n_i
 /* Train the model on n_pairs pairs (device FP32 fields on the net's grid;
  * pair_slice on the host gives the slice index of each pair) by Adam on the
  * mean squared error |G(u) - F(u)|^2 over all points of a batch.  loss_hist
- * (host, may be NULL) receives one mean loss per epoch. */
+ * (host, may be NULL) receives one mean loss per epoch.  Where the net's
+ * grid edge is a multiple of 16, the 16 -> 16 layers' forward and both
+ * gradients run on the tensor cores, whose completion waits are bounded:
+ * PARAREAL_E_TIMEOUT if one gave up (checked after every epoch; the
+ * context stays usable). */
 parareal_status parareal_train_coarse(parareal_ctx *ctx, const float *pairs_u, const float *pairs_f,
                                       const int *pair_slice, int n_pairs,
                                       const parareal_train_config *tc, double *loss_hist);
 
 /* One forward and backward pass without an update: the mean squared error
  * over `count` fields (device FP32, net grid) against `target`, and its
- * gradient (device, PARAREAL_MODEL_PARAMS floats).  slices: host, count ints. */
+ * gradient (device, PARAREAL_MODEL_PARAMS floats).  slices: host, count ints.
+ * PARAREAL_E_TIMEOUT as for parareal_train_coarse. */
 parareal_status parareal_coarse_model_grad(parareal_ctx *ctx, const float *u, const float *target,
                                            const int *slices, int count, float *grad_out,
                                            double *loss);
