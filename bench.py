@@ -503,9 +503,10 @@ def c4_learned_128(dev_index, steps=3, n_ics=63, epochs=20, batch=8, lr=1e-3, pi
     x 32 slices = 2016 pairs, `epochs` epochs on the tensor-core training
     kernels), evaluated as phase kernels on the coarse grid (and, as
     learned_composed, as one 9^3 kernel per slice), against Parareal with the
-    stencil propagator alone and the serial fine run.  All Parareal runs use
-    the difference form of the correction and run as one graph launch each
-    (parareal_iterate_device).  Times are CUDA events on
+    stencil propagator alone and the serial fine run; the stencil and the
+    phase-kernel learned G once more with pipelined iterations (two blocks).
+    All Parareal runs use the difference form of the correction and run as
+    one graph launch each (parareal_iterate_device).  Times are CUDA events on
     the contexts' stream; clocks are sampled over the whole
     comparison, training included."""
     import torch
@@ -513,11 +514,11 @@ def c4_learned_128(dev_index, steps=3, n_ics=63, epochs=20, batch=8, lr=1e-3, pi
     base, u0 = configs.fp32_128()
     n, N = base.n, base.n_slices
     nf = round(base.T / N / base.dt_fine)
-    mk = lambda kind, ev: native.Config.make(
+    mk = lambda kind, ev, pb=pipeline: native.Config.make(
         n, N, base.T, base.dt_fine, base.dt_coarse, base.coarse_factor, fine_dtype=native.F32,
         coarse_kind=kind, nu0=base.nu0, nu_amp=base.nu_amp, nu_omega=base.nu_omega,
         learned_skip=native.SKIP_STENCIL, learned_act=native.ACT_LINEAR,
-        correction_form=native.CORRECTION_DIFFERENCE, learned_eval=ev, pipeline_blocks=pipeline)
+        correction_form=native.CORRECTION_DIFFERENCE, learned_eval=ev, pipeline_blocks=pb)
     stream = torch.cuda.Stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -562,11 +563,17 @@ def c4_learned_128(dev_index, steps=3, n_ics=63, epochs=20, batch=8, lr=1e-3, pi
         u = torch.from_numpy(u0).cuda()
         torch.cuda.synchronize()
         # "learned": the phase-kernel evaluation; "learned_composed": the same
-        # operator as one 9^3 kernel on the fine grid
-        for name, kind, ev in (("stencil", native.COARSE_STENCIL, native.EVAL_LAYERS),
-                               ("learned", native.COARSE_LEARNED, native.EVAL_POLYPHASE),
-                               ("learned_composed", native.COARSE_LEARNED, native.EVAL_COMPOSED)):
-            c = native.Parareal(mk(kind, ev), stream=stream)
+        # operator as one 9^3 kernel on the fine grid; "*_pipelined": the next
+        # iteration's fine sweep started in two blocks of slices while the
+        # coarse chain runs (pipeline_blocks = 2), the same iterates
+        for name, kind, ev, pb in (("stencil", native.COARSE_STENCIL, native.EVAL_LAYERS, pipeline),
+                                   ("learned", native.COARSE_LEARNED, native.EVAL_POLYPHASE, pipeline),
+                                   ("learned_composed", native.COARSE_LEARNED, native.EVAL_COMPOSED, pipeline),
+                                   ("stencil_pipelined", native.COARSE_STENCIL, native.EVAL_LAYERS, 2),
+                                   ("learned_pipelined", native.COARSE_LEARNED, native.EVAL_POLYPHASE, 2)):
+            if pb == pipeline and name.endswith("_pipelined"):
+                continue
+            c = native.Parareal(mk(kind, ev, pb), stream=stream)
             c.autotune(TUNE_CACHE)
             if kind == native.COARSE_LEARNED:
                 c.set_coarse_model(w)
@@ -586,7 +593,8 @@ def c4_learned_128(dev_index, steps=3, n_ics=63, epochs=20, batch=8, lr=1e-3, pi
             g_ms, _ = timed(lambda: c.propagate(1, src, dst, 1, 1), 10)
             out[name] = {"k_star": int(k), "time_to_1e-6_ms": ms, "g_apply_ms": g_ms,
                          "glups_in_solve": sum(N - j for j in range(k)) * n ** 3 * nf / ms / 1e6,
-                         "final_defect": float(h[-1, 2]), "defects": [float(x) for x in h[:, 2]]}
+                         "final_defect": float(h[-1, 2]), "defects": [float(x) for x in h[:, 2]],
+                         "pipeline_blocks": pb}
             c.close()
     out["learned_over_stencil"] = out["learned"]["time_to_1e-6_ms"] / out["stencil"]["time_to_1e-6_ms"]
     out["learned_over_serial_fine"] = out["learned"]["time_to_1e-6_ms"] / out["serial_fine_ms"]
